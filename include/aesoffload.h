@@ -1,0 +1,254 @@
+/*
+ * aesoffload.h -- C ABI of the GB300 AES-CTR offload library (libaesoffload.so).
+ *
+ * The offload is the one the paper routes through each server's own
+ * concurrency (Sec. 3: submit the work to an executor, suspend the request,
+ * resume it on completion; Sec. 6 setup: "GPU AES" on its own CUDA stream,
+ * completion detected by polling).  The paper fixes neither mode nor key
+ * size; this library computes AES-128/192/256 (FIPS-197) in counter mode
+ * (NIST SP 800-38A Sec. 6.5) with the caller supplying the whole 16-byte
+ * initial counter block T_1, incremented as one 128-bit big-endian integer
+ * (SP 800-38A App. B.1, m = 128; wraps modulo 2^128).  Encryption and
+ * decryption are the same operation.
+ *
+ * Conventions shared by every call:
+ *   - Status codes: AES_OK (0), AES_PENDING (1, served mode only) or a
+ *     negative AES_E* code.  No call aborts or throws; CUDA errors become
+ *     AES_ECUDA and the CUDA error string is kept for aes_last_error().
+ *   - Payload pointers (in/out) are device pointers (cudaMalloc, or the
+ *     device alias of pinned host memory allocated with cudaHostAlloc /
+ *     registered with cudaHostRegister).  Both must be 16-byte aligned
+ *     (AES_EALIGN otherwise).  in == out (in place) is allowed; any other
+ *     overlap returns AES_EOVERLAP.  Bytes of out past len are never written.
+ *     The caller owns payload buffers and keeps them alive until the work is
+ *     complete (stream order, or AES_OK from offload_poll).
+ *   - Streams are passed as void* holding a cudaStream_t (NULL = the legacy
+ *     default stream).  Work is asynchronous on that stream.
+ *   - Key material and descriptor arrays are host memory, copied during the
+ *     call; the caller may reuse them as soon as the call returns.
+ *   - Every call acts on the CUDA device that is current on the calling
+ *     thread; an aes_ctx_t / plan / server stays bound to the device it was
+ *     created on.
+ */
+#ifndef AESOFFLOAD_H
+#define AESOFFLOAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define AES_OK 0
+#define AES_PENDING 1       /* served request not finished yet */
+#define AES_EINVAL (-1)     /* null / malformed argument */
+#define AES_EKEYBITS (-2)   /* key size not 128, 192 or 256 bits */
+#define AES_EALIGN (-3)     /* in/out not 16-byte aligned */
+#define AES_EOVERLAP (-4)   /* in and out overlap without being equal */
+#define AES_EAGAIN (-5)     /* served mode: no slot or HBM budget free now */
+#define AES_ETIMEOUT (-6)   /* a bounded wait ran out */
+#define AES_ECUDA (-7)      /* a CUDA runtime call failed */
+#define AES_ESTOPPED (-8)   /* served mode: the server is stopping/stopped */
+#define AES_ENOMEM (-9)     /* allocation failed */
+#define AES_ETOOBIG (-10)   /* a size exceeds a documented maximum */
+#define AES_EPTR (-11)      /* a payload pointer is not device-accessible */
+#define AES_EDESC (-12)     /* served mode: the device rejected the request */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *aes_strerror(int status);
+
+/* The last CUDA error text seen by this thread (static/thread-local storage,
+ * never NULL; "" when none). */
+const char *aes_last_error(void);
+
+/* Library version as 0xMMmmpp. */
+int aes_version(void);
+
+/* ------------------------------------------------------------ key contexts */
+
+/* Opaque key context: owns the device-resident key schedule of one key. */
+typedef struct aes_ctx_s *aes_ctx_t;
+
+/* Create a context for `key` (host pointer, bits/8 bytes), bits in
+ * {128, 192, 256}.  KeyExpansion (FIPS-197 Sec. 5.2) runs in a CUDA kernel
+ * on the current device and the 4*(Nr+1)-word schedule stays in device
+ * memory.  Synchronous (allocates and waits for the expansion).  Not for use
+ * inside stream capture.  Errors: AES_EINVAL (null out/key), AES_EKEYBITS,
+ * AES_ENOMEM, AES_ECUDA.  On error *out is set to NULL. */
+int aes_ctx_create(aes_ctx_t *out, const uint8_t *key, int bits);
+
+/* Release a context (NULL is a no-op).  The caller must ensure no work that
+ * uses it is still queued or running.  Returns AES_OK. */
+int aes_ctx_destroy(aes_ctx_t ctx);
+
+/* Key size in bits, or AES_EINVAL for a NULL ctx. */
+int aes_ctx_bits(aes_ctx_t ctx);
+
+/* Copy the device-expanded key schedule to host memory `w` (capacity `cap`
+ * bytes): 16*(Nr+1) bytes, word i of FIPS-197 Sec. 5.2 at w[4i..4i+3].
+ * Returns the number of bytes written, or AES_EINVAL / AES_ETOOBIG (cap too
+ * small) / AES_ECUDA.  Synchronous. */
+int aes_ctx_round_keys(aes_ctx_t ctx, uint8_t *w, size_t cap);
+
+/* ------------------------------------------------------- single-buffer CTR */
+
+/* Kernel variants for the block cipher (SubBytes/ShiftRows/MixColumns). */
+#define AES_VARIANT_AUTO 0      /* the tuned choice for (size, Nr) */
+#define AES_VARIANT_TTABLE 1    /* 32-way bank-replicated T-tables in shared memory */
+#define AES_VARIANT_BITSLICE 2  /* 32 blocks per thread, boolean circuit (LOP3) */
+
+/* Launch shape override (all-zero fields mean "use the tuned value"). */
+typedef struct {
+    int variant;        /* AES_VARIANT_* */
+    int threads;        /* CTA size: multiple of 32, 32..1024 */
+    int blocks_per_thread; /* T-table: 16-byte blocks each thread keeps in flight (1, 2 or 4) */
+    int ctas;           /* grid size; 0 = enough for the data, capped at SMs x occupancy */
+} aes_launch_t;
+
+/* out[0..len) = in[0..len) xor AES-CTR keystream from T_1 = iv (host
+ * pointer, 16 bytes), SP 800-38A Sec. 6.5: block j (0-based) is xored with
+ * CIPH_K(T_1 + j mod 2^128); a final partial block uses the leading bytes of
+ * its keystream block.  One kernel launch on `stream` (none when len == 0).
+ * Errors: AES_EINVAL (null ctx/iv, null in/out with len > 0), AES_EALIGN,
+ * AES_EOVERLAP, AES_EPTR (a pointer the GPU cannot address), AES_ECUDA. */
+int aes_ctr(aes_ctx_t ctx, const uint8_t *iv, const void *in, void *out, size_t len,
+            void *stream);
+
+/* aes_ctr with an explicit launch shape (autotuner, tests, sweeps); `cfg`
+ * NULL behaves like aes_ctr.  Extra error: AES_EINVAL for a shape outside the
+ * documented ranges. */
+int aes_ctr_ex(aes_ctx_t ctx, const uint8_t *iv, const void *in, void *out, size_t len,
+               void *stream, const aes_launch_t *cfg);
+
+/* ----------------------------------------------------------- batched varlen */
+
+/* One request of a batch: its own key context, initial counter and length. */
+typedef struct {
+    aes_ctx_t ctx;
+    uint8_t iv[16];
+    const void *in;
+    void *out;
+    size_t len;
+} aes_desc_t;
+
+/* Options of the persistent batch kernel (all-zero = tuned defaults). */
+typedef struct {
+    int variant;        /* AES_VARIANT_* (AUTO picks T-table) */
+    int threads;        /* CTA size */
+    int tile_blocks;    /* 16-byte blocks per work tile (multiple of threads) */
+    int ctas;           /* persistent CTAs; 0 = one per SM (x occupancy) */
+    uint32_t tile_order_seed; /* nonzero: tiles are claimed in a seeded
+                                 pseudo-random permutation (testing aid; the
+                                 result must not change) */
+} aes_batch_opts_t;
+
+/* Encrypt n independent requests in ONE persistent-kernel launch on
+ * `stream`: the requests are cut into tiles of 16-byte blocks and the CTAs
+ * claim tiles through a device atomic (work stealing).  Any mix of key sizes
+ * and lengths; each request follows aes_ctr's contract.  The descriptor
+ * table is uploaded from host memory inside the call (descs may be reused on
+ * return).  n == 0 is a no-op.  Errors: AES_EINVAL (n < 0, null descs, a
+ * NULL ctx), AES_EALIGN / AES_EOVERLAP / AES_EPTR for the first bad request,
+ * AES_ETOOBIG (n > AES_BATCH_MAX), AES_ENOMEM, AES_ECUDA. */
+#define AES_BATCH_MAX (1 << 20)
+int aes_ctr_batch(const aes_desc_t *descs, int n, void *stream);
+int aes_ctr_batch_ex(const aes_desc_t *descs, int n, void *stream, const aes_batch_opts_t *opts);
+
+/* A prepared batch: the descriptor table lives on the device and the launch
+ * (counter reset + persistent kernel) is captured once into a CUDA graph, so
+ * repeated encryption of the same request layout costs one graph launch.
+ * Payload contents may change between launches; pointers, lengths, keys and
+ * IVs are fixed at creation. */
+typedef struct aes_batch_plan_s *aes_batch_plan_t;
+int aes_batch_plan_create(aes_batch_plan_t *out, const aes_desc_t *descs, int n,
+                          const aes_batch_opts_t *opts);
+int aes_batch_plan_launch(aes_batch_plan_t plan, void *stream);
+/* Payload bytes covered by one launch of the plan. */
+int64_t aes_batch_plan_bytes(aes_batch_plan_t plan);
+int aes_batch_plan_destroy(aes_batch_plan_t plan);
+
+/* --------------------------------------------------------------- autotuner */
+
+/* Time the candidate launch shapes of aes_ctr (per size bucket and key
+ * size) and of the batch kernel on the current device, on scratch buffers
+ * the call allocates and frees, and keep the fastest for AES_VARIANT_AUTO.
+ * Synchronous; takes roughly a second.  `path` (may be NULL) names a JSON
+ * file the table is written to. */
+int aes_autotune(const char *path);
+
+/* Load a table written by aes_autotune (ignored if it was measured on a
+ * device with another name or SM count).  AES_EINVAL if unreadable. */
+int aes_autotune_load(const char *path);
+
+/* Describe the shape AES_VARIANT_AUTO picks for (len, bits). */
+int aes_tuned_shape(size_t len, int bits, aes_launch_t *out);
+
+/* ---------------------------------------------------------------- served mode */
+
+/* A resident persistent kernel polls a descriptor queue in pinned, mapped
+ * host memory, so a request costs no kernel launch: offload_submit writes a
+ * descriptor and returns a ticket at once (submit + suspend), the kernel
+ * encrypts the request's tiles alongside every other request in flight
+ * (continuous batching), and the CTA finishing the last tile raises the
+ * request's completion flag, which offload_poll reads (resume). */
+typedef struct offload_server_s *offload_server_t;
+
+typedef struct {
+    int slots;              /* requests in flight at most (<= 65536); 0 = 1024 */
+    int max_keys;           /* resident key schedules; 0 = 64 */
+    uint64_t hbm_budget;    /* bytes of payload in flight at most (in + out,
+                               in-place counted once); 0 = unlimited */
+    int ctas;               /* resident CTAs; 0 = SM count - 4 */
+    int threads;            /* CTA size; 0 = tuned */
+    int tile_blocks;        /* 16-byte blocks per tile; 0 = tuned */
+    uint32_t idle_timeout_us; /* resident kernel exits after this long with no
+                                 work (relaunched on the next submit); 0 = 200000 */
+} offload_cfg_t;
+
+typedef struct {
+    uint64_t submitted, completed, rejected_eagain, device_errors, relaunches;
+    uint64_t bytes_completed;
+    uint32_t kernel_status;    /* last exit status of the resident kernel */
+    int running;               /* resident kernel currently launched */
+} offload_stats_t;
+
+/* Start a server on the current device: allocates the key store, the mapped
+ * descriptor queue and device state, and launches the resident kernel on a
+ * stream of its own.  Errors: AES_EINVAL, AES_ENOMEM, AES_ECUDA. */
+int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg);
+
+/* Expand `key` into resident key slot *slot_out (device kernel, FIPS-197
+ * Sec. 5.2).  Thread-safe.  AES_ETOOBIG when all max_keys slots are used. */
+int offload_key_register(offload_server_t srv, const uint8_t *key, int bits, int *slot_out);
+
+/* Submit one request; never blocks on the GPU.  On AES_OK *ticket identifies
+ * it for offload_poll.  Thread-safe (any number of submitter threads).
+ * Errors: AES_EAGAIN (no slot or budget free: back-pressure), AES_EINVAL
+ * (bad key slot, null iv/in/out with len > 0), AES_EALIGN, AES_EOVERLAP,
+ * AES_ETOOBIG (len > 16 GiB), AES_ESTOPPED, AES_ECUDA. */
+int offload_submit(offload_server_t srv, int key_slot, const uint8_t *iv, const void *in,
+                   void *out, size_t len, uint64_t *ticket);
+
+/* AES_OK once the request is complete and its output visible to the host
+ * and to later GPU work (the ticket is then released; polling it again gives
+ * AES_EINVAL), AES_PENDING while in flight, AES_EDESC if the device rejected
+ * the descriptor, AES_EINVAL for an unknown ticket.  Thread-safe. */
+int offload_poll(offload_server_t srv, uint64_t ticket);
+
+/* Poll until done or `timeout_us` passes (AES_ETIMEOUT, ticket stays live). */
+int offload_wait(offload_server_t srv, uint64_t ticket, uint64_t timeout_us);
+
+int offload_server_stats(offload_server_t srv, offload_stats_t *out);
+
+/* Raise the stop flag, wait (bounded, 5 s) for the resident kernel to exit,
+ * and free everything.  Requests still in flight are abandoned.  Returns
+ * AES_ETIMEOUT if the kernel did not exit in time (resources are then leaked
+ * rather than freed under a running kernel). */
+int offload_server_destroy(offload_server_t srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AESOFFLOAD_H */

@@ -1,0 +1,342 @@
+"""Python binding of libaesoffload.so (ctypes; argument marshalling only).
+
+Every computation happens in the library's CUDA kernels.  PyTorch is used
+only to hand over device pointers (``tensor.data_ptr()``) and streams
+(``torch.cuda.Stream.cuda_stream``); plain integers work as well.  If the
+library has not been built the first call raises -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+# status codes (include/aesoffload.h)
+AES_OK = 0
+AES_PENDING = 1
+AES_EINVAL = -1
+AES_EKEYBITS = -2
+AES_EALIGN = -3
+AES_EOVERLAP = -4
+AES_EAGAIN = -5
+AES_ETIMEOUT = -6
+AES_ECUDA = -7
+AES_ESTOPPED = -8
+AES_ENOMEM = -9
+AES_ETOOBIG = -10
+AES_EPTR = -11
+AES_EDESC = -12
+
+VARIANT_AUTO = 0
+VARIANT_TTABLE = 1
+VARIANT_BITSLICE = 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AesError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        msg = strerror(code)
+        extra = last_error()
+        super().__init__(f"{where}: {msg}" + (f" ({extra})" if extra and code == AES_ECUDA else ""))
+
+
+class LaunchShape(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("threads", ctypes.c_int),
+                ("blocks_per_thread", ctypes.c_int), ("ctas", ctypes.c_int)]
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("iv", ctypes.c_uint8 * 16), ("inp", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("len", ctypes.c_size_t)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("threads", ctypes.c_int), ("tile_blocks", ctypes.c_int),
+                ("ctas", ctypes.c_int), ("tile_order_seed", ctypes.c_uint32)]
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_keys", ctypes.c_int), ("hbm_budget", ctypes.c_uint64),
+                ("ctas", ctypes.c_int), ("threads", ctypes.c_int), ("tile_blocks", ctypes.c_int),
+                ("idle_timeout_us", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected_eagain", ctypes.c_uint64), ("device_errors", ctypes.c_uint64),
+                ("relaunches", ctypes.c_uint64), ("bytes_completed", ctypes.c_uint64),
+                ("kernel_status", ctypes.c_uint32), ("running", ctypes.c_int)]
+
+
+_SIGS = {
+    "aes_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "aes_last_error": (ctypes.c_char_p, []),
+    "aes_version": (ctypes.c_int, []),
+    "aes_ctx_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int]),
+    "aes_ctx_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "aes_ctx_bits": (ctypes.c_int, [ctypes.c_void_p]),
+    "aes_ctx_round_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "aes_ctr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_size_t, ctypes.c_void_p]),
+    "aes_ctr_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(LaunchShape)]),
+    "aes_ctr_batch": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int, ctypes.c_void_p]),
+    "aes_ctr_batch_ex": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.POINTER(BatchOpts)]),
+    "aes_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Desc),
+                                             ctypes.c_int, ctypes.POINTER(BatchOpts)]),
+    "aes_batch_plan_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "aes_batch_plan_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "aes_batch_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "aes_autotune": (ctypes.c_int, [ctypes.c_char_p]),
+    "aes_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "aes_tuned_shape": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(LaunchShape)]),
+    "offload_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ServerCfg)]),
+    "offload_key_register": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
+    "offload_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]),
+    "offload_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "offload_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]),
+    "offload_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    "offload_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(_build.LIB):
+                    raise RuntimeError(
+                        "libaesoffload.so is not built; run paper_2607_02630_gb300.build.build() "
+                        "(needs nvcc) -- there is no CPU fallback")
+                L = ctypes.CDLL(_build.LIB)
+                for name, (res, args) in _SIGS.items():
+                    f = getattr(L, name, None)
+                    if f is None:
+                        continue
+                    f.restype = res
+                    f.argtypes = args
+                _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().aes_strerror(code).decode()
+
+
+def last_error() -> str:
+    return lib().aes_last_error().decode()
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise AesError(rc, where)
+    return rc
+
+
+def ptr(x) -> int:
+    """Device address of a torch tensor, or an int passed through."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def stream_handle(s) -> int:
+    if s is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _bytes16(iv) -> ctypes.Array:
+    b = bytes(bytearray(iv if isinstance(iv, (bytes, bytearray)) else bytes(memoryview(iv).tobytes())))
+    if len(b) != 16:
+        raise ValueError("iv must be 16 bytes")
+    return (ctypes.c_uint8 * 16).from_buffer_copy(b)
+
+
+def _keybuf(key) -> bytes:
+    return bytes(bytearray(key if isinstance(key, (bytes, bytearray)) else memoryview(key).tobytes()))
+
+
+class Context:
+    """A device-resident AES key schedule (aes_ctx_create)."""
+
+    def __init__(self, key, bits: int):
+        kb = _keybuf(key)
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(kb, max(len(kb), 1))
+        _check(lib().aes_ctx_create(ctypes.byref(h), buf, int(bits)), "aes_ctx_create")
+        self.handle = h.value
+        self.bits = int(bits)
+
+    def round_keys(self) -> bytes:
+        out = ctypes.create_string_buffer(240)
+        n = _check(lib().aes_ctx_round_keys(self.handle, out, 240), "aes_ctx_round_keys")
+        return out.raw[:n]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().aes_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ctr_status(ctx: Context, iv, src, dst, nbytes: int, stream=None, variant: int = 0,
+               threads: int = 0, blocks_per_thread: int = 0, ctas: int = 0) -> int:
+    """aes_ctr_ex returning the raw status code."""
+    shape = LaunchShape(variant, threads, blocks_per_thread, ctas)
+    return lib().aes_ctr_ex(ctx.handle if ctx else None, _bytes16(iv), ptr(src), ptr(dst),
+                            int(nbytes), stream_handle(stream), ctypes.byref(shape))
+
+
+def ctr(ctx: Context, iv, src, dst, nbytes: int | None = None, stream=None, **shape) -> None:
+    """dst[:n] = src[:n] xor AES-CTR keystream (asynchronous on `stream`)."""
+    if nbytes is None:
+        nbytes = src.numel() * src.element_size()
+    _check(ctr_status(ctx, iv, src, dst, nbytes, stream, **shape), "aes_ctr")
+
+
+def _descs(requests):
+    arr = (Desc * max(len(requests), 1))()
+    for i, (ctx, iv, src, dst, n) in enumerate(requests):
+        arr[i].ctx = ctx.handle
+        arr[i].iv = _bytes16(iv)
+        arr[i].inp = ptr(src)
+        arr[i].out = ptr(dst)
+        arr[i].len = int(n)
+    return arr
+
+
+def batch_status(requests, stream=None, variant=0, threads=0, tile_blocks=0, ctas=0,
+                 tile_order_seed=0) -> int:
+    arr = _descs(requests)
+    opts = BatchOpts(variant, threads, tile_blocks, ctas, tile_order_seed)
+    return lib().aes_ctr_batch_ex(arr, len(requests), stream_handle(stream), ctypes.byref(opts))
+
+
+def batch(requests, stream=None, **opts) -> None:
+    """One persistent launch over requests = [(ctx, iv, src, dst, nbytes), ...]."""
+    _check(batch_status(requests, stream, **opts), "aes_ctr_batch")
+
+
+class BatchPlan:
+    """aes_batch_plan_*: a device-resident descriptor table + captured CUDA graph."""
+
+    def __init__(self, requests, variant=0, threads=0, tile_blocks=0, ctas=0, tile_order_seed=0):
+        arr = _descs(requests)
+        opts = BatchOpts(variant, threads, tile_blocks, ctas, tile_order_seed)
+        h = ctypes.c_void_p()
+        _check(lib().aes_batch_plan_create(ctypes.byref(h), arr, len(requests), ctypes.byref(opts)),
+               "aes_batch_plan_create")
+        self.handle = h.value
+
+    @property
+    def nbytes(self) -> int:
+        return int(lib().aes_batch_plan_bytes(self.handle))
+
+    def launch(self, stream=None) -> None:
+        _check(lib().aes_batch_plan_launch(self.handle, stream_handle(stream)), "aes_batch_plan_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().aes_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(path: str | None = None) -> None:
+    _check(lib().aes_autotune(path.encode() if path else None), "aes_autotune")
+
+
+def autotune_load(path: str) -> None:
+    _check(lib().aes_autotune_load(path.encode()), "aes_autotune_load")
+
+
+def tuned_shape(nbytes: int, bits: int) -> dict:
+    s = LaunchShape()
+    _check(lib().aes_tuned_shape(int(nbytes), int(bits), ctypes.byref(s)), "aes_tuned_shape")
+    return {"variant": s.variant, "threads": s.threads, "blocks_per_thread": s.blocks_per_thread,
+            "ctas": s.ctas}
+
+
+class Server:
+    """Served mode: a resident kernel polling mapped descriptors (offload_*)."""
+
+    def __init__(self, slots=0, max_keys=0, hbm_budget=0, ctas=0, threads=0, tile_blocks=0,
+                 idle_timeout_us=0):
+        cfg = ServerCfg(slots, max_keys, hbm_budget, ctas, threads, tile_blocks, idle_timeout_us)
+        h = ctypes.c_void_p()
+        _check(lib().offload_server_create(ctypes.byref(h), ctypes.byref(cfg)), "offload_server_create")
+        self.handle = h.value
+
+    def key_register(self, key, bits: int) -> int:
+        slot = ctypes.c_int(-1)
+        kb = _keybuf(key)
+        buf = ctypes.create_string_buffer(kb, max(len(kb), 1))
+        _check(lib().offload_key_register(self.handle, buf, int(bits), ctypes.byref(slot)),
+               "offload_key_register")
+        return slot.value
+
+    def submit_status(self, key_slot: int, iv, src, dst, nbytes: int):
+        t = ctypes.c_uint64(0)
+        rc = lib().offload_submit(self.handle, int(key_slot), _bytes16(iv), ptr(src), ptr(dst),
+                                  int(nbytes), ctypes.byref(t))
+        return rc, t.value
+
+    def submit(self, key_slot: int, iv, src, dst, nbytes: int) -> int:
+        rc, t = self.submit_status(key_slot, iv, src, dst, nbytes)
+        _check(rc, "offload_submit")
+        return t
+
+    def poll(self, ticket: int) -> int:
+        return lib().offload_poll(self.handle, ctypes.c_uint64(ticket))
+
+    def wait(self, ticket: int, timeout_us: int = 5_000_000) -> int:
+        return lib().offload_wait(self.handle, ctypes.c_uint64(ticket), ctypes.c_uint64(timeout_us))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().offload_server_stats(self.handle, ctypes.byref(s)), "offload_server_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self) -> int:
+        rc = 0
+        if getattr(self, "handle", None):
+            rc = lib().offload_server_destroy(self.handle)
+            self.handle = None
+        return rc
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,62 @@
+// internal.h -- host-side interfaces between the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace aesrt {
+
+constexpr int kMaxRoundKeyWords = 60;  // 4 * (14 + 1)
+
+// Parameters of one single-key CTR launch.  Passed by value (kernel
+// parameter space), so the round keys are constant-bank operands.
+struct CtrParams {
+    const uint4 *in;
+    uint4 *out;
+    uint64_t len;           // payload bytes
+    uint64_t iv_hi, iv_lo;  // initial counter block as big-endian halves
+    const uint32_t *te0;    // 256-word T-table seed (device)
+    uint32_t rk[kMaxRoundKeyWords];  // round keys, little-endian column words
+};
+
+struct CtrShape {
+    int variant;  // 1 = T-table, 2 = bitsliced
+    int threads;
+    int nb;       // T-table blocks per thread per pass (1, 2, 4)
+    int ctas;     // 0 = derive
+};
+
+// Device tables and key expansion (tables.cu).
+cudaError_t launch_te0_init(uint32_t *te0, cudaStream_t stream);
+cudaError_t launch_key_expand(const uint8_t *keys, const int32_t *bits, const uint32_t *te0,
+                              uint32_t *w, int n, cudaStream_t stream);
+
+// Single-buffer CTR (ctr.cu).
+cudaError_t ctr_set_attributes();  // once per device
+int ctr_max_ctas(const CtrShape &s, int nsm);
+int ctr_ctas_for(uint64_t nblocks, const CtrShape &s, int nsm);
+cudaError_t launch_ctr(const CtrParams &p, int nr, const CtrShape &s, int nsm, cudaStream_t stream);
+
+// Batched varlen CTR (batch.cu).
+struct BatchReq {        // one request, device-side descriptor (64 bytes)
+    const uint4 *in;
+    uint4 *out;
+    uint64_t len;
+    uint64_t iv_hi, iv_lo;
+    const uint4 *rk;     // device round keys (4*(Nr+1) words as uint4 per round)
+    uint32_t nr;
+    uint32_t pad;
+    uint64_t tile_begin; // prefix sum of tiles before this request
+};
+static_assert(sizeof(BatchReq) == 64, "descriptor is one 64-byte line");
+
+struct BatchShape {
+    int variant;
+    int threads;
+    int tile_blocks;
+    int ctas;
+};
+
+cudaError_t batch_set_attributes();
+
+}  // namespace aesrt

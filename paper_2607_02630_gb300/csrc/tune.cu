@@ -1,0 +1,240 @@
+// tune.cu -- launch-shape table and the autotuner.
+//
+// For every (Nr, length bucket) the table holds the CTR kernel variant and
+// shape to use when the caller asks for AES_VARIANT_AUTO.  Defaults come
+// from occupancy arithmetic; aes_autotune() replaces them with the fastest
+// candidate measured on this device with CUDA events.
+#include "../../include/aesoffload.h"
+#include "internal.h"
+#include "runtime.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace aesrt {
+
+int len_bucket(size_t len)
+{
+    int b = 0;
+    while (b + 1 < kLenBuckets && ((size_t)1 << (b + 1)) <= len)
+        ++b;
+    return b;
+}
+
+static int nr_index(int nr) { return nr == 10 ? 0 : (nr == 12 ? 1 : 2); }
+
+int validate_ctr_shape(const CtrShape &s)
+{
+    if (s.variant == AES_VARIANT_BITSLICE)
+        return s.threads == 128 && s.ctas >= 0 ? AES_OK : AES_EINVAL;
+    if (s.variant != AES_VARIANT_TTABLE)
+        return AES_EINVAL;
+    if (s.threads < 32 || s.threads > 1024 || (s.threads & 31))
+        return AES_EINVAL;
+    if (s.nb != 1 && s.nb != 2 && s.nb != 4)
+        return AES_EINVAL;
+    return s.ctas >= 0 ? AES_OK : AES_EINVAL;
+}
+
+// Default: one T-table CTA per SM; as many threads as keep every SM busy.
+static CtrShape default_shape(int nsm, int bucket)
+{
+    const uint64_t nblocks = ((uint64_t)1 << bucket) / 16 + 1;
+    CtrShape s{AES_VARIANT_TTABLE, 256, 1, 0};
+    if (nblocks >= (uint64_t)nsm * 1024 * 2 * 4)
+        s = CtrShape{AES_VARIANT_TTABLE, 1024, 2, 0};
+    else if (nblocks >= (uint64_t)nsm * 1024)
+        s = CtrShape{AES_VARIANT_TTABLE, 1024, 1, 0};
+    else if (nblocks >= (uint64_t)nsm * 512)
+        s = CtrShape{AES_VARIANT_TTABLE, 512, 1, 0};
+    return s;
+}
+
+void tune_defaults(DeviceState &st)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int b = 0; b < kLenBuckets; ++b)
+            st.ctr_tuned[i][b] = default_shape(st.nsm, b);
+    st.batch_tuned = BatchShape{AES_VARIANT_TTABLE, 1024, 8192, 0};
+}
+
+CtrShape tuned_ctr_shape(const DeviceState &st, size_t len, int nr)
+{
+    return st.ctr_tuned[nr_index(nr)][len_bucket(len)];
+}
+
+}  // namespace aesrt
+
+using namespace aesrt;
+
+namespace {
+
+float time_ctr(aes_ctx_t ctx, const uint8_t *iv, void *buf_in, void *buf_out, size_t len,
+               const aes_launch_t &cfg, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps)
+{
+    for (int w = 0; w < 2; ++w)
+        if (aes_ctr_ex(ctx, iv, buf_in, buf_out, len, s, &cfg) != AES_OK)
+            return -1.f;
+    std::vector<float> t;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(a, s);
+        aes_ctr_ex(ctx, iv, buf_in, buf_out, len, s, &cfg);
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess)
+            return -1.f;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+}
+
+}  // namespace
+
+extern "C" {
+
+int aes_tuned_shape(size_t len, int bits, aes_launch_t *out)
+{
+    if (!out || (bits != 128 && bits != 192 && bits != 256))
+        return AES_EINVAL;
+    DeviceState *st = nullptr;
+    int rc = device_state(&st);
+    if (rc)
+        return rc;
+    const CtrShape s = tuned_ctr_shape(*st, len, bits / 32 + 6);
+    out->variant = s.variant;
+    out->threads = s.threads;
+    out->blocks_per_thread = s.nb;
+    out->ctas = ctr_ctas_for((len + 15) / 16, s, st->nsm);
+    return AES_OK;
+}
+
+int aes_autotune(const char *path)
+{
+    DeviceState *st = nullptr;
+    int rc = device_state(&st);
+    if (rc)
+        return rc;
+    const int lo_b = 12, hi_b = 28;  // 4 KiB .. 256 MiB
+    const size_t maxlen = (size_t)1 << hi_b;
+    void *in = nullptr, *out = nullptr;
+    cudaError_t e = cudaMalloc(&in, maxlen);
+    if (!e)
+        e = cudaMalloc(&out, maxlen);
+    if (e) {
+        cudaFree(in);
+        return e == cudaErrorMemoryAllocation ? AES_ENOMEM : cuda_fail(e, "autotune alloc");
+    }
+    cudaMemset(in, 0x5a, maxlen);
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const uint8_t key[32] = {1, 2, 3};
+    const uint8_t iv[16] = {9};
+    const aes_launch_t cands[] = {
+        {AES_VARIANT_TTABLE, 256, 1, 0},  {AES_VARIANT_TTABLE, 512, 1, 0},
+        {AES_VARIANT_TTABLE, 1024, 1, 0}, {AES_VARIANT_TTABLE, 512, 2, 0},
+        {AES_VARIANT_TTABLE, 1024, 2, 0}, {AES_VARIANT_TTABLE, 1024, 4, 0},
+        {AES_VARIANT_BITSLICE, 128, 1, 0},
+    };
+    const int bits_list[3] = {128, 192, 256};
+    for (int ki = 0; ki < 3 && rc == AES_OK; ++ki) {
+        aes_ctx_t ctx = nullptr;
+        if ((rc = aes_ctx_create(&ctx, key, bits_list[ki])))
+            break;
+        for (int bk = lo_b; bk <= hi_b; ++bk) {
+            const size_t len = (size_t)1 << bk;
+            const int reps = bk <= 20 ? 15 : (bk <= 24 ? 7 : 3);
+            float best = 1e30f;
+            CtrShape pick = st->ctr_tuned[ki][bk];
+            for (const aes_launch_t &c : cands) {
+                const float ms = time_ctr(ctx, iv, in, out, len, c, s, a, b, reps);
+                if (ms > 0 && ms < best) {
+                    best = ms;
+                    pick = CtrShape{c.variant, c.threads, c.blocks_per_thread, 0};
+                }
+            }
+            st->ctr_tuned[ki][bk] = pick;
+        }
+        for (int bk = 0; bk < lo_b; ++bk)
+            st->ctr_tuned[ki][bk] = st->ctr_tuned[ki][lo_b];
+        for (int bk = hi_b + 1; bk < kLenBuckets; ++bk)
+            st->ctr_tuned[ki][bk] = st->ctr_tuned[ki][hi_b];
+        aes_ctx_destroy(ctx);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(s);
+    cudaFree(in);
+    cudaFree(out);
+    if (rc)
+        return rc;
+    if (path) {
+        FILE *f = std::fopen(path, "w");
+        if (!f)
+            return AES_EINVAL;
+        std::fprintf(f, "{\"device\": \"%s\", \"sms\": %d, \"ctr\": [\n", st->name, st->nsm);
+        for (int ki = 0; ki < 3; ++ki)
+            for (int bk = 0; bk < kLenBuckets; ++bk) {
+                const CtrShape &c = st->ctr_tuned[ki][bk];
+                std::fprintf(f, "  [%d, %d, %d, %d, %d]%s\n", ki, bk, c.variant, c.threads, c.nb,
+                             (ki == 2 && bk == kLenBuckets - 1) ? "" : ",");
+            }
+        std::fprintf(f, "],\n\"batch\": [%d, %d, %d]}\n", st->batch_tuned.variant,
+                     st->batch_tuned.threads, st->batch_tuned.tile_blocks);
+        std::fclose(f);
+    }
+    return AES_OK;
+}
+
+int aes_autotune_load(const char *path)
+{
+    if (!path)
+        return AES_EINVAL;
+    DeviceState *st = nullptr;
+    int rc = device_state(&st);
+    if (rc)
+        return rc;
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return AES_EINVAL;
+    char line[512];
+    int sms = -1;
+    char name[256] = {0};
+    int nread = 0;
+    CtrShape table[3][kLenBuckets];
+    std::memcpy(table, st->ctr_tuned, sizeof(table));
+    BatchShape bs = st->batch_tuned;
+    while (std::fgets(line, sizeof(line), f)) {
+        int ki, bk, v, t, nb;
+        if (std::sscanf(line, "{\"device\": \"%255[^\"]\", \"sms\": %d", name, &sms) == 2)
+            continue;
+        if (std::sscanf(line, " [%d, %d, %d, %d, %d]", &ki, &bk, &v, &t, &nb) == 5) {
+            if (ki < 0 || ki > 2 || bk < 0 || bk >= kLenBuckets)
+                continue;
+            CtrShape c{v, t, nb, 0};
+            if (validate_ctr_shape(c) == AES_OK) {
+                table[ki][bk] = c;
+                ++nread;
+            }
+            continue;
+        }
+        if (std::sscanf(line, "\"batch\": [%d, %d, %d]", &v, &t, &nb) == 3)
+            bs = BatchShape{v, t, nb, 0};
+    }
+    std::fclose(f);
+    if (sms != st->nsm || std::strcmp(name, st->name) != 0)
+        return AES_OK;  // measured elsewhere: keep the current table
+    if (nread == 0)
+        return AES_EINVAL;
+    std::memcpy(st->ctr_tuned, table, sizeof(table));
+    st->batch_tuned = bs;
+    return AES_OK;
+}
+
+}  // extern "C"

@@ -18,3 +18,25 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="session")
+def aes(cuda):
+    from paper_2607_02630_gb300 import aesoffload, build
+
+    build.build()
+    aesoffload.lib()
+    return aesoffload
+
+
+@pytest.fixture(scope="session")
+def ncpu():
+    return max(1, os.cpu_count() or 1)

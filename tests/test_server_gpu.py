@@ -1,0 +1,246 @@
+"""Served mode: resident kernel polling mapped descriptors (offload_*).
+
+Checks bit-exact results against the oracle, that every request gives the
+same bytes alone and in a concurrent mix, admission (slots, HBM budget),
+tickets, idle exit + relaunch and the stop path.  Every device wait in the
+resident kernel is bounded, so none of these can hang the GPU; host waits
+use offload_wait with a timeout.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_02630_gb300 import workloads as W
+
+from gpu_util import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+WAIT_US = 10_000_000
+
+
+@pytest.fixture()
+def server(aes):
+    srv = aes.Server(slots=64, max_keys=16, ctas=32, tile_blocks=2048, idle_timeout_us=500_000)
+    yield srv
+    assert srv.close() == aes.AES_OK
+
+
+def arena(torch, g, sizes):
+    pad = [(n + 255) // 256 * 256 + 256 for n in sizes]
+    offs = np.concatenate([[0], np.cumsum(pad)[:-1]]).astype(np.int64)
+    payload = W.random_bytes(g, int(sum(pad)))
+    return payload, offs, to_dev(torch, payload), to_dev(torch, np.zeros(0, np.uint8), pad=int(sum(pad)))
+
+
+def test_served_results_match_oracle(cuda, aes, server, ncpu):
+    g = W.rng(60)
+    keys = [(W.random_bytes(g, b // 8), b) for b in (128, 256, 192, 128)]
+    slots = [server.key_register(k.tobytes(), b) for k, b in keys]
+    sizes = [0, 1, 15, 16, 17, 4096, 65536 + 3, 1 << 20, (1 << 20) + 9, 3 << 20, 8 << 20] + \
+        [int(x) for x in W.served_sizes(20, seed=61) if x <= (1 << 20)]
+    payload, offs, src, dst = arena(cuda, g, sizes)
+    tickets = []
+    for i, n in enumerate(sizes):
+        iv = W.random_bytes(g, 16)
+        k = i % len(keys)
+        o = int(offs[i])
+        t = server.submit(slots[k], iv.tobytes(), src.data_ptr() + o, dst.data_ptr() + o, n)
+        tickets.append((t, k, iv, o, n))
+    for t, k, iv, o, n in tickets:
+        assert server.wait(t, WAIT_US) == aes.AES_OK
+    out = to_host(dst)
+    for t, k, iv, o, n in tickets:
+        key, bits = keys[k]
+        np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, bits, iv, payload[o: o + n], ncpu))
+        assert (out[o + n: o + n + 16] == 0xA5).all()
+    st = server.stats()
+    assert st["completed"] == len(sizes) and st["device_errors"] == 0
+
+
+def test_same_result_alone_and_in_the_mix(cuda, aes, server):
+    """Each request's bytes do not depend on what else is on the GPU."""
+    g = W.rng(62)
+    keys = [(W.random_bytes(g, b // 8), b) for b in (128, 256)]
+    slots = [server.key_register(k.tobytes(), b) for k, b in keys]
+    sizes = [int(x) for x in W.served_sizes(48, seed=63)]
+    sizes = [min(n, 2 << 20) for n in sizes]
+    payload, offs, src, dst = arena(cuda, g, sizes)
+    ivs = [W.random_bytes(g, 16).tobytes() for _ in sizes]
+    # alone: one request in flight at a time
+    alone = []
+    for i, n in enumerate(sizes):
+        o = int(offs[i])
+        t = server.submit(slots[i % 2], ivs[i], src.data_ptr() + o, dst.data_ptr() + o, n)
+        assert server.wait(t, WAIT_US) == aes.AES_OK
+        alone.append(to_host(dst[o: o + n]).copy())
+    # in the mix: all submitted back to back, completing out of order
+    dst.fill_(0xA5)
+    order = list(g.permutation(len(sizes)))
+    tickets = []
+    for i in order:
+        o = int(offs[i])
+        tickets.append((i, server.submit(slots[i % 2], ivs[i], src.data_ptr() + o, dst.data_ptr() + o,
+                                         sizes[i])))
+    for i, t in tickets:
+        assert server.wait(t, WAIT_US) == aes.AES_OK
+    for i, n in enumerate(sizes):
+        o = int(offs[i])
+        np.testing.assert_array_equal(to_host(dst[o: o + n]), alone[i], err_msg=f"request {i}")
+
+
+def test_poll_right_after_submit_and_ticket_rules(cuda, aes, server):
+    slot = server.key_register(bytes(16), 128)
+    buf = cuda.zeros(1 << 20, dtype=cuda.uint8, device="cuda")
+    t = server.submit(slot, bytes(16), buf.data_ptr(), buf.data_ptr(), 1 << 20)
+    assert server.poll(t) in (aes.AES_PENDING, aes.AES_OK)  # never unknown
+    assert server.wait(t, WAIT_US) in (aes.AES_OK, aes.AES_EINVAL)
+    assert server.poll(t) == aes.AES_EINVAL  # released
+    assert server.poll(0) == aes.AES_EINVAL
+    assert server.poll(t ^ (1 << 40)) == aes.AES_EINVAL
+
+
+def test_submit_argument_errors(cuda, aes, server):
+    slot = server.key_register(bytes(32), 256)
+    buf = cuda.zeros(1 << 16, dtype=cuda.uint8, device="cuda")
+    p = buf.data_ptr()
+    assert server.submit_status(slot + 5, bytes(16), p, p, 64)[0] == aes.AES_EINVAL  # unregistered
+    assert server.submit_status(-1, bytes(16), p, p, 64)[0] == aes.AES_EINVAL
+    assert server.submit_status(slot, bytes(16), p + 4, p + 4096, 64)[0] == aes.AES_EALIGN
+    assert server.submit_status(slot, bytes(16), p, p + 16, 64)[0] == aes.AES_EOVERLAP
+    assert server.submit_status(slot, bytes(16), p, p, 1 << 50)[0] == aes.AES_ETOOBIG
+    rc, t = server.submit_status(slot, bytes(16), 0, 0, 0)  # empty request completes
+    assert rc == aes.AES_OK and server.wait(t, WAIT_US) == aes.AES_OK
+
+
+def test_slots_exhausted_gives_eagain(cuda, aes):
+    srv = aes.Server(slots=4, max_keys=2, ctas=2, idle_timeout_us=500_000)
+    slot = srv.key_register(bytes(16), 128)
+    buf = cuda.zeros(64 << 20, dtype=cuda.uint8, device="cuda")
+    p = buf.data_ptr()
+    n = 8 << 20
+    tickets = []
+    saw_again = False
+    for i in range(6):
+        rc, t = srv.submit_status(slot, bytes(16), p + i * n, p + i * n, n)
+        if rc == aes.AES_EAGAIN:
+            saw_again = True
+        else:
+            assert rc == aes.AES_OK
+            tickets.append(t)
+    assert len(tickets) <= 4 and saw_again  # ~0.3 ms per 8 MiB request on 2 CTAs
+    for t in tickets:
+        assert srv.wait(t, WAIT_US) == aes.AES_OK
+    rc, t = srv.submit_status(slot, bytes(16), p, p, n)  # slots free again
+    assert rc == aes.AES_OK and srv.wait(t, WAIT_US) == aes.AES_OK
+    assert srv.close() == aes.AES_OK
+
+
+def test_hbm_budget_back_pressure(cuda, aes):
+    n = 8 << 20
+    budget = 3 * n  # three in-place 8 MiB requests
+    srv = aes.Server(slots=64, max_keys=2, ctas=4, hbm_budget=budget, idle_timeout_us=500_000)
+    slot = srv.key_register(bytes(16), 128)
+    buf = cuda.zeros(12 * n, dtype=cuda.uint8, device="cuda")
+    p = buf.data_ptr()
+    # out-of-place counts in + out: 2 * 2n > budget can never be admitted
+    assert srv.submit_status(slot, bytes(16), p, p + 4 * n, 2 * n)[0] == aes.AES_ETOOBIG
+    accepted, rejected = [], 0
+    for i in range(12):
+        rc, t = srv.submit_status(slot, bytes(16), p + i * n, p + i * n, n)
+        if rc == aes.AES_EAGAIN:
+            rejected += 1
+        else:
+            assert rc == aes.AES_OK
+            accepted.append(t)
+    assert rejected > 0 and len(accepted) >= 3
+    for t in accepted:
+        assert srv.wait(t, WAIT_US) == aes.AES_OK
+    st = srv.stats()
+    assert st["rejected_eagain"] == rejected
+    rc, t = srv.submit_status(slot, bytes(16), p, p, n)
+    assert rc == aes.AES_OK and srv.wait(t, WAIT_US) == aes.AES_OK
+    assert srv.close() == aes.AES_OK
+
+
+def test_idle_exit_then_relaunch(cuda, aes, ncpu):
+    srv = aes.Server(slots=8, max_keys=2, ctas=8, idle_timeout_us=20_000)
+    key = np.arange(16, dtype=np.uint8)
+    slot = srv.key_register(key.tobytes(), 128)
+    g = W.rng(64)
+    data = W.random_bytes(g, 1 << 20)
+    src = to_dev(cuda, data)
+    dst = to_dev(cuda, np.zeros(0, np.uint8), pad=data.size)
+    iv = W.random_bytes(g, 16)
+    t = srv.submit(slot, iv.tobytes(), src, dst, data.size)
+    assert srv.wait(t, WAIT_US) == aes.AES_OK
+    deadline = time.time() + 5
+    while srv.stats()["running"] and time.time() < deadline:
+        time.sleep(0.01)
+    st = srv.stats()
+    assert st["running"] == 0 and (st["kernel_status"] & 2), st  # exited on idle timeout
+    dst.fill_(0)
+    t = srv.submit(slot, iv.tobytes(), src, dst, data.size)
+    assert srv.wait(t, WAIT_US) == aes.AES_OK
+    assert srv.stats()["relaunches"] >= 1
+    np.testing.assert_array_equal(to_host(dst), oracle.ctr_mt(key, 128, iv, data, ncpu))
+    assert srv.close() == aes.AES_OK
+
+
+def test_stop_with_work_in_flight(cuda, aes):
+    srv = aes.Server(slots=32, max_keys=2, ctas=16, idle_timeout_us=2_000_000)
+    slot = srv.key_register(bytes(16), 128)
+    buf = cuda.zeros(256 << 20, dtype=cuda.uint8, device="cuda")
+    p = buf.data_ptr()
+    for i in range(32):
+        srv.submit_status(slot, bytes(16), p + i * (8 << 20), p + i * (8 << 20), 8 << 20)
+    t0 = time.time()
+    assert srv.close() == aes.AES_OK
+    assert time.time() - t0 < 5
+
+
+def test_eight_submitter_threads(cuda, aes, ncpu):
+    srv = aes.Server(slots=128, max_keys=8, ctas=64, tile_blocks=2048, idle_timeout_us=1_000_000)
+    g = W.rng(65)
+    keys = [(W.random_bytes(g, b // 8), b) for b in (128, 256) * 4]
+    slots = [srv.key_register(k.tobytes(), b) for k, b in keys]
+    per_thread = 24
+    sizes = [int(min(x, 1 << 20)) for x in W.served_sizes(8 * per_thread, seed=66)]
+    payload, offs, src, dst = arena(cuda, g, sizes)
+    ivs = [W.random_bytes(g, 16).tobytes() for _ in sizes]
+    errors = []
+
+    def worker(tid):
+        try:
+            mine = []
+            for j in range(per_thread):
+                i = tid * per_thread + j
+                o = int(offs[i])
+                while True:
+                    rc, t = srv.submit_status(slots[i % 8], ivs[i], src.data_ptr() + o, dst.data_ptr() + o,
+                                              sizes[i])
+                    if rc != aes.AES_EAGAIN:
+                        break
+                assert rc == aes.AES_OK, rc
+                mine.append(t)
+            for t in mine:
+                assert srv.wait(t, WAIT_US) == aes.AES_OK
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    th = [threading.Thread(target=worker, args=(k,)) for k in range(8)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join(60)
+    assert not errors, errors
+    out = to_host(dst)
+    for i, n in enumerate(sizes):
+        o = int(offs[i])
+        key, bits = keys[i % 8]
+        want = oracle.ctr(key, bits, np.frombuffer(ivs[i], np.uint8), payload[o: o + n])
+        np.testing.assert_array_equal(out[o: o + n], want, err_msg=f"request {i}")
+    assert srv.close() == aes.AES_OK
