@@ -1,0 +1,453 @@
+"""Benchmark of the batched AES-CTR offload on GB300 (one JSON line on stdout).
+
+Workload (the batched varlen case): 4096 requests, each with its own random
+key (AES-128 / AES-256, 50/50) and IV, lengths log-uniform on [1 KiB, 8 MiB],
+25% with a 1..15-byte tail; about 3.8 GB of payload per step.  A step is one
+launch of the persistent batch kernel over all 4096 requests (a CUDA-graph
+plan: counter reset + kernel).  Inputs (3.8 GB) are far larger than L2
+(129 MB), so no L2 flush is needed between steps.
+
+Also reported: the same requests as 4096 single-buffer launches (per-call),
+p50/p99 latency of a 1 MiB offload through the per-call path (aes_ctr +
+cudaEventQuery polling) and the served path (offload_submit + offload_poll),
+the end-to-end figure with payloads in pinned host memory, the roofline of
+the dominant kernel, SM clocks sampled during the timed region, and the CPU
+oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own replica of the workload on
+its own GPU (independent requests, no data-path collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_02630_gb300 import workloads as W  # noqa: E402
+
+METRIC = "AES-CTR GB/s (% roofline) batched vs per-call; p50/p99 1 MiB offload µs"
+UNIT = "GB/s"
+WORKLOAD = "batched varlen AES-CTR: 4096 requests, own key (AES-128/256 50/50) and IV each, " \
+           "lengths log-uniform 1 KiB..8 MiB, 25% with 1..15-byte tails"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [s for s, p in zip(sm, pw)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(pw) if pw else None}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------- oracle leg
+
+def oracle_sample(w, budget_s: float, nthreads: int):
+    """Time the CPU oracle on a prefix of the requests of `w` sized to take
+    about budget_s seconds (calibrated on a 4 MiB probe)."""
+    import oracle
+
+    oracle.build()
+    probe = w.payload[: 4 << 20]
+    key = w.key_of(0)
+    t0 = time.perf_counter()
+    oracle.ctr_mt(key, int(w.bits[0]), w.ivs[0], probe, nthreads)
+    rate = probe.size / max(time.perf_counter() - t0, 1e-6)
+    target = rate * budget_s
+    idx, acc = [], 0
+    for i in range(w.n):
+        if acc >= target:
+            break
+        idx.append(i)
+        acc += int(w.lengths[i])
+    return idx, acc
+
+
+def run_oracle(w, idx, nthreads: int) -> float:
+    import oracle
+
+    t0 = time.perf_counter()
+    for i in idx:
+        o, n = int(w.offsets[i]), int(w.lengths[i])
+        oracle.ctr_mt(w.key_of(i), int(w.bits[i]), w.ivs[i], w.payload[o: o + n], nthreads)
+    return time.perf_counter() - t0
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return 0
+    nthreads = os.cpu_count() or 1
+    w = W.batch_varlen(seed=W.SEED_BASE + 3)
+    per_step_s = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    idx, nbytes = oracle_sample(w, per_step_s, nthreads)
+    for _ in range(args.warmup):
+        run_oracle(w, idx[:1], nthreads)
+    times = [run_oracle(w, idx, nthreads) for _ in range(args.steps)]
+    total = sum(times)
+    value = nbytes * args.steps / total / 1e9
+    sample = f"first {len(idx)} of 4096 requests ({nbytes / 1e6:.1f} MB) per step, oracle_ctr_mt"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "global_batch": 4096, "seq_len": None,
+                                        "parallelism": f"replicas{args.gpus}"},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------- our arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="only the headline step timing")
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, ws, rank)
+
+    import torch
+
+    from paper_2607_02630_gb300 import aesoffload as A
+    from paper_2607_02630_gb300 import build as libbuild
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    libbuild.build()
+    A.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = int(stream.cuda_stream)
+
+    # ---- workload, resident in HBM
+    w = W.batch_varlen(seed=W.SEED_BASE + 3 + 1000 * rank)
+    src = torch.from_numpy(w.payload).to(dev)
+    dst = torch.empty(w.arena_bytes, dtype=torch.uint8, device=dev)
+    ctxs = [A.Context(w.key_of(i).tobytes(), int(w.bits[i])) for i in range(w.n)]
+    reqs = [(ctxs[i], w.ivs[i].tobytes(), src.data_ptr() + int(w.offsets[i]),
+             dst.data_ptr() + int(w.offsets[i]), int(w.lengths[i])) for i in range(w.n)]
+    plan = A.BatchPlan(reqs)
+    step_bytes = plan.nbytes
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- headline: K plan launches, events around each on the launch stream
+    for _ in range(args.warmup):
+        plan.launch(sh)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for a, b in ev:
+            a.record(stream)
+            plan.launch(sh)
+            b.record(stream)
+        t_end.record(stream)
+        stream.synchronize()
+    barrier()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    per_launch = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    if dist:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = ws * step_bytes * args.steps / elapsed / 1e9
+    clocks = clk.summary()
+
+    # ---- roofline of the batch kernel (on-chip shared-memory lookup bound)
+    pk, pk_kind = peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    lookups = sum(((int(n) + 15) // 16) * 16 * (int(b) // 32 + 6) for n, b in zip(w.lengths, w.bits))
+    lookups_per_s_peak = 32.0 * nsm * sm_max_mhz * 1e6  # one conflict-free LDS.32 warp-op / clk / SM
+    floor_s = lookups / lookups_per_s_peak
+    roof_gbs = step_bytes / floor_s / 1e9
+    launch_s = statistics.mean(per_launch)
+    achieved = step_bytes / launch_s / 1e9
+    hbm_roof = float(pk.get("hbm_gbs", 6784.5)) / 2.0  # 2 bytes moved per payload byte
+    roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(roof_gbs, 2), "unit": "GB/s",
+                "frac": round(achieved / roof_gbs, 4), "traffic": None,
+                "peak_basis": f"shared-memory lookups: 32/clk/SM x {nsm} SMs x {sm_max_mhz:.0f} MHz, "
+                              f"16*Nr lookups per 16-byte block ({pk_kind} clock)",
+                "hbm_payload_roof_gbs": round(hbm_roof, 1),
+                "frac_of_hbm_roof": round(achieved / hbm_roof, 4),
+                "kernel": "batch_ttable_kernel"}
+    traffic = os.path.join(ROOT, "profiles", "traffic_batch_ttable_kernel.json")
+    if os.path.exists(traffic):
+        try:
+            with open(traffic) as f:
+                tr = json.load(f)
+            roofline["traffic"] = tr.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+
+    extras = {}
+    if not args.no_extras:
+        extras = run_extras(A, torch, dev, stream, sh, w, ctxs, reqs, src, dst, step_bytes, args)
+
+    # ---- end to end: payloads in pinned host memory, read/written by the kernel over C2C
+    e2e = run_e2e(A, torch, w, ctxs, args, sh, stream, dist, ws)
+
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_extras:
+            nthreads = os.cpu_count() or 1
+            idx, nbytes = oracle_sample(w, args.oracle_seconds, nthreads)
+            secs = run_oracle(w, idx, nthreads)
+            cpu = {"value": round(nbytes / secs / 1e9, 6), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                   "sample": f"first {len(idx)} of the 4096 requests ({nbytes / 1e6:.1f} MB), "
+                             f"oracle_ctr_mt on {nthreads} threads, {secs:.1f} s"}
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 4096 * ws, "seq_len": None,
+                       "parallelism": f"replicas{ws}", "step_bytes": step_bytes,
+                       "l2": "no flush: 3.8 GB of inputs per step, far above the 129 MB L2",
+                       "launch": "aes_batch_plan_launch (CUDA graph: counter reset + persistent kernel)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_extras(A, torch, dev, stream, sh, w, ctxs, reqs, src, dst, step_bytes, args):
+    out = {}
+    # per-call: the same 4096 requests, one aes_ctr launch each, one stream
+    def per_call():
+        for r in reqs:
+            A.ctr(r[0], r[1], r[2], r[3], r[4], stream=sh)
+
+    per_call()
+    stream.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    a.record(stream)
+    for _ in range(reps):
+        per_call()
+    b.record(stream)
+    stream.synchronize()
+    pc = step_bytes * reps / (a.elapsed_time(b) / 1e3) / 1e9
+    # one aes_ctr_batch call (uploads its descriptor table each call) for comparison
+    A.batch(reqs, stream=sh)
+    stream.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        A.batch(reqs, stream=sh)
+    b.record(stream)
+    stream.synchronize()
+    one_shot = step_bytes * reps / (a.elapsed_time(b) / 1e3) / 1e9
+    out["per_call"] = {"value": round(pc, 3), "unit": UNIT, "launches_per_step": len(reqs),
+                       "how": "4096 aes_ctr calls on one stream, tuned shapes"}
+    out["batch_one_shot"] = {"value": round(one_shot, 3), "unit": UNIT,
+                             "how": "aes_ctr_batch (descriptor upload + launch each call)"}
+
+    # latency of a 1 MiB offload: per-call path with cudaEventQuery polling
+    g = W.rng(W.SEED_BASE + 1)
+    one = W.single_buffer(1 << 20, 128, seed=W.SEED_BASE + 1)
+    s_in = torch.from_numpy(one.payload).to(dev)
+    s_out = torch.empty_like(s_in)
+    ctx = A.Context(one.key.tobytes(), 128)
+    iv = one.iv.tobytes()
+    evq = torch.cuda.Event()
+    lat = []
+    for i in range(50 + 2000):
+        t0 = time.perf_counter()
+        A.ctr(ctx, iv, s_in, s_out, 1 << 20, stream=sh)
+        evq.record(stream)
+        while not evq.query():
+            pass
+        if i >= 50:
+            lat.append((time.perf_counter() - t0) * 1e6)
+    dev_ms = []
+    for i in range(200):
+        a.record(stream)
+        A.ctr(ctx, iv, s_in, s_out, 1 << 20, stream=sh)
+        b.record(stream)
+        stream.synchronize()
+        dev_ms.append(a.elapsed_time(b))
+    out["latency_1mib_per_call_us"] = {"p50": round(float(np.percentile(lat, 50)), 2),
+                                       "p99": round(float(np.percentile(lat, 99)), 2),
+                                       "device_us_median": round(statistics.median(dev_ms) * 1e3, 2),
+                                       "gbs_device": round((1 << 20) / (statistics.median(dev_ms) / 1e3) / 1e9, 2),
+                                       "how": "aes_ctr + cudaEventQuery poll, one in flight, 2000 calls"}
+    # served path: submit + poll, one in flight
+    srv = A.Server(slots=64, max_keys=4, idle_timeout_us=2_000_000)
+    try:
+        slot = srv.key_register(one.key.tobytes(), 128)
+        lat_s = []
+        for i in range(50 + 2000):
+            t0 = time.perf_counter()
+            t = srv.submit(slot, iv, s_in, s_out, 1 << 20)
+            while srv.poll(t) == A.AES_PENDING:
+                pass
+            if i >= 50:
+                lat_s.append((time.perf_counter() - t0) * 1e6)
+        out["latency_1mib_served_us"] = {"p50": round(float(np.percentile(lat_s, 50)), 2),
+                                         "p99": round(float(np.percentile(lat_s, 99)), 2),
+                                         "how": "offload_submit + offload_poll, one in flight, 2000 requests"}
+        # served throughput: all 4096 requests through the resident kernel
+        keyslots = {}
+        t0 = time.perf_counter()
+        tickets = []
+        srv2 = A.Server(slots=4096, max_keys=64, idle_timeout_us=2_000_000)
+        try:
+            for i in range(64):
+                keyslots[i] = srv2.key_register(w.key_of(i).tobytes(), int(w.bits[i]))
+            t0 = time.perf_counter()
+            for i, r in enumerate(reqs):
+                tickets.append(srv2.submit(keyslots[i % 64], r[1], r[2], r[3], r[4]))
+            for t in tickets:
+                assert srv2.wait(t, 30_000_000) == A.AES_OK
+            dt = time.perf_counter() - t0
+            out["served_throughput"] = {"value": round(step_bytes / dt / 1e9, 3), "unit": UNIT,
+                                        "how": "4096 requests submitted back to back (keys from a 64-key set)"}
+        finally:
+            srv2.close()
+    finally:
+        srv.close()
+    return out
+
+
+def run_e2e(A, torch, w, ctxs, args, sh, stream, dist, ws):
+    """Same metric with payloads in pinned host memory: the kernel reads the
+    plaintext from and writes the ciphertext to host memory (NVLink-C2C),
+    so each step moves step_bytes host->device and step_bytes device->host."""
+    h_in = torch.from_numpy(w.payload).pin_memory()
+    h_out = torch.empty(w.arena_bytes, dtype=torch.uint8).pin_memory()
+    reqs = [(ctxs[i], w.ivs[i].tobytes(), h_in.data_ptr() + int(w.offsets[i]),
+             h_out.data_ptr() + int(w.offsets[i]), int(w.lengths[i])) for i in range(w.n)]
+    plan = A.BatchPlan(reqs)
+    nbytes = plan.nbytes
+    steps = max(3, min(args.steps, 60))
+    for _ in range(max(1, min(args.warmup, 3))):
+        plan.launch(sh)
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        plan.launch(sh)
+    b.record(stream)
+    stream.synchronize()
+    secs = a.elapsed_time(b) / 1e3
+    if dist:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    plan.close()
+    return {"value": round(ws * nbytes * steps / secs / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": steps,
+            "how": "aes_batch_plan_launch on pinned host buffers (zero-copy over NVLink-C2C)"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())
