@@ -156,6 +156,26 @@ typedef struct {
 int aes_ctr_batch(const aes_desc_t *descs, int n, void *stream);
 int aes_ctr_batch_ex(const aes_desc_t *descs, int n, void *stream, const aes_batch_opts_t *opts);
 
+/* aes_ctr_batch for callers that cannot allocate device memory -- e.g. a
+ * process whose HBM is entirely reserved by another framework's pool, a
+ * latency-critical path that must not pay for cudaMalloc/cudaFree (which can
+ * synchronise the device), or a runtime that forbids allocation after
+ * start-up.  The paper has no counterpart: this is a deployment variant of
+ * the batched launch.  Same contract and result as aes_ctr_batch, but the
+ * call allocates nothing: its scratch (descriptor table + claim counter)
+ * lives in one static device array of AES_NOALLOC_MAX_REQUESTS descriptors
+ * (about 64 KiB) that every GPU loading the library keeps until exit.  The
+ * key contexts must already exist on the current device (AES_EINVAL if no
+ * context was ever created on it).  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call reuses the same array and leaves
+ * its contents behind: calls whose work may overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Errors: those of aes_ctr_batch, and AES_ETOOBIG when n exceeds
+ * AES_NOALLOC_MAX_REQUESTS. */
+#define AES_NOALLOC_MAX_REQUESTS 1024
+int aes_ctr_batch_noalloc(const aes_desc_t *descs, int n, void *stream);
+
 /* A prepared batch: the descriptor table lives on the device and the launch
  * (counter reset + persistent kernel) is captured once into a CUDA graph, so
  * repeated encryption of the same request layout costs one graph launch.

@@ -63,6 +63,20 @@ int device_state(DeviceState **out)
     return AES_OK;
 }
 
+// The current device's state if an earlier call already set it up; never
+// initialises (and so never allocates).
+int device_state_ready(DeviceState **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices || !g_devices[dev].ready.load(std::memory_order_acquire))
+        return AES_EINVAL;
+    *out = &g_devices[dev];
+    return AES_OK;
+}
+
 // A payload pointer must be device-addressable on `dev`: device or managed
 // memory of that device, or pinned host memory (its device alias is used).
 int resolve_ptr(const void *p, int dev, const void **dptr)

@@ -33,6 +33,7 @@ struct DeviceState {
 extern thread_local char g_last_error[256];
 int cuda_fail(cudaError_t e, const char *where);
 int device_state(DeviceState **out);
+int device_state_ready(DeviceState **out);
 int resolve_ptr(const void *p, int dev, const void **dptr);
 int check_payload(const void *in, const void *out, size_t len, int dev, const void **din, void **dout);
 void iv_halves(const uint8_t *iv, uint64_t *hi, uint64_t *lo);
