@@ -119,6 +119,52 @@ def dist_env():
     return ws, rank, local
 
 
+KERNEL_SOURCES = ["paper_2607_02630_gb300/csrc/batch.cu", "paper_2607_02630_gb300/csrc/tile.cuh",
+                  "paper_2607_02630_gb300/csrc/aes_ttable.cuh", "paper_2607_02630_gb300/csrc/common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "batch_ttable_kernel.traffic.txt")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(step_bytes: int):
+    """DRAM bytes (read + write) per launch of the batch kernel from the
+    committed ncu capture, scaled from the captured case to this launch by
+    payload bytes; None if the kernel changed since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.loads(f.readline())
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_src_sha") != kernel_source_hash():
+        return None
+    per_byte = rec["dram_bytes"] / rec["payload_bytes"]
+    return int(per_byte * step_bytes)
+
+
+def ttable_lookups(w) -> int:
+    """Shared-memory lookups the T-table method needs for workload w: 16*Nr
+    per 16-byte block, except that counter-mode caching replaces the 32
+    lookups of rounds 1-2 by 5 per block plus 27 per 256-block counter group."""
+    total = 0
+    for n, b, iv in zip(w.lengths, w.bits, w.ivs):
+        nb = (int(n) + 15) // 16
+        if nb == 0:
+            continue
+        nr = int(b) // 32 + 6
+        v0 = int(iv[15])
+        groups = ((v0 + nb - 1) >> 8) + 1
+        total += nb * (16 * nr - 27) + 27 * groups
+    return total
+
+
 # --------------------------------------------------------------------- oracle leg
 
 def oracle_sample(w, budget_s: float, nthreads: int):
@@ -188,6 +234,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="only the headline step timing")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the pinned-host end-to-end leg")
+    ap.add_argument("--requests", type=int, default=4096,
+                    help="requests per step (4096 = the benchmark workload; fewer only for profiler captures)")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     args = ap.parse_args()
     ws, rank, local = dist_env()
@@ -212,7 +261,7 @@ def main():
     sh = int(stream.cuda_stream)
 
     # ---- workload, resident in HBM
-    w = W.batch_varlen(seed=W.SEED_BASE + 3 + 1000 * rank)
+    w = W.batch_varlen(n=args.requests, seed=W.SEED_BASE + 3 + 1000 * rank)
     src = torch.from_numpy(w.payload).to(dev)
     dst = torch.empty(w.arena_bytes, dtype=torch.uint8, device=dev)
     ctxs = [A.Context(w.key_of(i).tobytes(), int(w.bits[i])) for i in range(w.n)]
@@ -256,8 +305,8 @@ def main():
     pk, pk_kind = peaks()
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    lookups = sum(((int(n) + 15) // 16) * 16 * (int(b) // 32 + 6) for n, b in zip(w.lengths, w.bits))
-    lookups_per_s_peak = 32.0 * nsm * sm_max_mhz * 1e6  # one conflict-free LDS.32 warp-op / clk / SM
+    lookups = ttable_lookups(w)
+    lookups_per_s_peak = 32.0 * nsm * sm_max_mhz * 1e6  # one 128-byte shared-memory wavefront / clk / SM
     floor_s = lookups / lookups_per_s_peak
     roof_gbs = step_bytes / floor_s / 1e9
     launch_s = statistics.mean(per_launch)
@@ -265,26 +314,21 @@ def main():
     hbm_roof = float(pk.get("hbm_gbs", 6784.5)) / 2.0  # 2 bytes moved per payload byte
     roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(roof_gbs, 2), "unit": "GB/s",
                 "frac": round(achieved / roof_gbs, 4), "traffic": None,
-                "peak_basis": f"shared-memory lookups: 32/clk/SM x {nsm} SMs x {sm_max_mhz:.0f} MHz, "
-                              f"16*Nr lookups per 16-byte block ({pk_kind} clock)",
+                "peak_basis": f"T-table lookups at one 128-byte shared-memory wavefront (32 lookups) per clk "
+                              f"per SM x {nsm} SMs x {sm_max_mhz:.0f} MHz ({pk_kind} max clock); "
+                              f"{lookups / 1e9:.3f} G lookups per step (16*Nr per block, rounds 1-2 "
+                              f"counter-cached: 5 per block + 27 per 256-block counter group)",
                 "hbm_payload_roof_gbs": round(hbm_roof, 1),
                 "frac_of_hbm_roof": round(achieved / hbm_roof, 4),
                 "kernel": "batch_ttable_kernel"}
-    traffic = os.path.join(ROOT, "profiles", "traffic_batch_ttable_kernel.json")
-    if os.path.exists(traffic):
-        try:
-            with open(traffic) as f:
-                tr = json.load(f)
-            roofline["traffic"] = tr.get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            pass
+    roofline["traffic"] = captured_traffic(step_bytes)
 
     extras = {}
     if not args.no_extras:
         extras = run_extras(A, torch, dev, stream, sh, w, ctxs, reqs, src, dst, step_bytes, args)
 
     # ---- end to end: payloads in pinned host memory, read/written by the kernel over C2C
-    e2e = run_e2e(A, torch, w, ctxs, args, sh, stream, dist, ws)
+    e2e = None if args.no_e2e else run_e2e(A, torch, w, ctxs, args, sh, stream, dist, ws)
 
     if rank == 0:
         cpu = None
@@ -300,7 +344,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": 4096 * ws, "seq_len": None,
+            "config": {"workload": WORKLOAD if args.requests == 4096 else f"{args.requests} requests of: " + WORKLOAD,
+                       "global_batch": args.requests * ws, "seq_len": None,
                        "parallelism": f"replicas{ws}", "step_bytes": step_bytes,
                        "l2": "no flush: 3.8 GB of inputs per step, far above the 129 MB L2",
                        "launch": "aes_batch_plan_launch (CUDA graph: counter reset + persistent kernel)"},

@@ -137,7 +137,7 @@ typedef struct {
 typedef struct {
     int variant;        /* AES_VARIANT_* (AUTO picks T-table) */
     int threads;        /* CTA size */
-    int tile_blocks;    /* 16-byte blocks per work tile (multiple of threads) */
+    int tile_blocks;    /* 16-byte blocks per work tile: a multiple of 256 (whole counter groups) */
     int ctas;           /* persistent CTAs; 0 = one per SM (x occupancy) */
     uint32_t tile_order_seed; /* nonzero: tiles are claimed in a seeded
                                  pseudo-random permutation (testing aid; the
@@ -221,8 +221,8 @@ typedef struct {
     uint64_t hbm_budget;    /* bytes of payload in flight at most (in + out,
                                in-place counted once); 0 = unlimited */
     int ctas;               /* resident CTAs; 0 = SM count - 4 */
-    int threads;            /* CTA size; 0 = tuned */
-    int tile_blocks;        /* 16-byte blocks per tile; 0 = tuned */
+    int threads;            /* CTA size, multiple of 32, <= 512; 0 = 512 */
+    int tile_blocks;        /* 16-byte blocks per tile, multiple of 256; 0 = 1024 */
     uint32_t idle_timeout_us; /* resident kernel exits after this long with no
                                  work (relaunched on the next submit); 0 = 200000 */
 } offload_cfg_t;

@@ -81,26 +81,17 @@ struct RkShared {
     __device__ __forceinline__ uint4 get(int r) const { return w[r]; }
 };
 
-// Encrypt NB blocks held as s[b][0..3] (little-endian column words) in
-// place: Nr rounds, initial AddRoundKey included.
-template <int NR, int NB, class RK>
-__device__ __forceinline__ void encrypt(uint32_t (&s)[NB][4], const uint8_t *tab, const Lanes &ln,
-                                        const RK &rk)
+// Rounds R0..NR-1 (full) and the final round NR on NB blocks held as
+// s[b][0..3] (little-endian column words), in place.  The state passed in is
+// the output of round R0 - 1.
+template <int R0, int NR, int NB, class RK>
+__device__ __forceinline__ void rounds(uint32_t (&s)[NB][4], const uint8_t *tab, const Lanes &ln,
+                                       const RK &rk)
 {
     const uint8_t *tabA = tab;
     const uint8_t *tabB = tab + kRegionBytes;
-    {
-        const uint4 k = rk.get(0);
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            s[b][0] ^= k.x;
-            s[b][1] ^= k.y;
-            s[b][2] ^= k.z;
-            s[b][3] ^= k.w;
-        }
-    }
-#pragma unroll
-    for (int r = 1; r < NR; ++r) {
+    for (int r = R0; r < NR; ++r) {
         const uint4 k = rk.get(r);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -136,6 +127,79 @@ __device__ __forceinline__ void encrypt(uint32_t (&s)[NB][4], const uint8_t *tab
             }
         }
     }
+}
+
+// Encrypt NB blocks held as s[b][0..3] in place: initial AddRoundKey, then
+// Nr rounds.
+template <int NR, int NB, class RK>
+__device__ __forceinline__ void encrypt(uint32_t (&s)[NB][4], const uint8_t *tab, const Lanes &ln,
+                                        const RK &rk)
+{
+    const uint4 k = rk.get(0);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        s[b][0] ^= k.x;
+        s[b][1] ^= k.y;
+        s[b][2] ^= k.z;
+        s[b][3] ^= k.w;
+    }
+    rounds<1, NR, NB>(s, tab, ln, rk);
+}
+
+// Counter-mode caching.  The 256 counter blocks T = G*256 + L (L = 0..255)
+// of one counter group share bytes 0..14, so after AddRoundKey only byte 15
+// (row 3 of column 3, through Te3 into output column 0) varies in round 1:
+// round 1 gives columns (P0 ^ Te3[L ^ k15], C1, C2, C3) with P0, C1..C3 fixed
+// for the group.  In round 2 the varying column 0 feeds exactly one lookup of
+// each output column (row r of column 0 reaches column -r mod 4), so round 2
+// is Q_c ^ (one lookup) with Q0..Q3 fixed for the group.  A block then needs 5
+// lookups for rounds 1-2 instead of 32; the group constants cost 27 lookups
+// once per group.
+struct Group {
+    uint32_t p0, c1, c2, c3, q0, q1, q2, q3, k15;
+};
+
+// base: the group's first counter block (byte 15 = 0) as column words.
+template <class RK>
+__device__ __forceinline__ Group group_consts(const uint32_t base[4], const uint8_t *tab, const Lanes &ln,
+                                              const RK &rk)
+{
+    const uint8_t *A = tab;                 // Te0 (lane sel s0), Te1 (s1)
+    const uint8_t *B = tab + kRegionBytes;  // Te2 (s0), Te3 (s1)
+    const uint4 k0 = rk.get(0), k1 = rk.get(1), k2 = rk.get(2);
+    const uint32_t s0 = base[0] ^ k0.x, s1 = base[1] ^ k0.y, s2 = base[2] ^ k0.z, s3 = base[3] ^ k0.w;
+    Group g;
+    g.k15 = k0.w >> 24;
+    g.p0 = lds(A, off<0>(s0, ln.s0)) ^ lds(A, off<1>(s1, ln.s1)) ^ lds(B, off<2>(s2, ln.s0)) ^ k1.x;
+    g.c1 = lds(A, off<0>(s1, ln.s0)) ^ lds(A, off<1>(s2, ln.s1)) ^ lds(B, off<2>(s3, ln.s0)) ^
+           lds(B, off<3>(s0, ln.s1)) ^ k1.y;
+    g.c2 = lds(A, off<0>(s2, ln.s0)) ^ lds(A, off<1>(s3, ln.s1)) ^ lds(B, off<2>(s0, ln.s0)) ^
+           lds(B, off<3>(s1, ln.s1)) ^ k1.z;
+    g.c3 = lds(A, off<0>(s3, ln.s0)) ^ lds(A, off<1>(s0, ln.s1)) ^ lds(B, off<2>(s1, ln.s0)) ^
+           lds(B, off<3>(s2, ln.s1)) ^ k1.w;
+    g.q0 = lds(A, off<1>(g.c1, ln.s1)) ^ lds(B, off<2>(g.c2, ln.s0)) ^ lds(B, off<3>(g.c3, ln.s1)) ^ k2.x;
+    g.q1 = lds(A, off<0>(g.c1, ln.s0)) ^ lds(A, off<1>(g.c2, ln.s1)) ^ lds(B, off<2>(g.c3, ln.s0)) ^ k2.y;
+    g.q2 = lds(A, off<0>(g.c2, ln.s0)) ^ lds(A, off<1>(g.c3, ln.s1)) ^ lds(B, off<3>(g.c1, ln.s1)) ^ k2.z;
+    g.q3 = lds(A, off<0>(g.c3, ln.s0)) ^ lds(B, off<2>(g.c1, ln.s0)) ^ lds(B, off<3>(g.c2, ln.s1)) ^ k2.w;
+    return g;
+}
+
+// Keystream of NB blocks of one group, L[b] = the blocks' low counter bytes.
+template <int NR, int NB, class RK>
+__device__ __forceinline__ void encrypt_group(uint32_t (&s)[NB][4], const uint32_t (&L)[NB], const Group &g,
+                                              const uint8_t *tab, const Lanes &ln, const RK &rk)
+{
+    const uint8_t *A = tab;
+    const uint8_t *B = tab + kRegionBytes;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const uint32_t r10 = g.p0 ^ lds(B, off<0>(L[b] ^ g.k15, ln.s1));  // Te3[byte 15]
+        s[b][0] = g.q0 ^ lds(A, off<0>(r10, ln.s0));                      // Te0[r10.b0]
+        s[b][1] = g.q1 ^ lds(B, off<3>(r10, ln.s1));                      // Te3[r10.b3]
+        s[b][2] = g.q2 ^ lds(B, off<2>(r10, ln.s0));                      // Te2[r10.b2]
+        s[b][3] = g.q3 ^ lds(A, off<1>(r10, ln.s1));                      // Te1[r10.b1]
+    }
+    rounds<3, NR, NB>(s, tab, ln, rk);
 }
 
 }  // namespace aestt

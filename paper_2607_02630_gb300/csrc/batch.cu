@@ -1,12 +1,15 @@
 // batch.cu -- many independent AES-CTR requests in one persistent launch.
 //
 // Every request (own key schedule, initial counter and length) is cut into
-// tiles of `tile_blocks` 16-byte blocks.  A host-built table maps each tile
-// to its request; CTAs (one per SM, T-tables filled once per CTA) claim tiles
-// through one device atomic counter until none are left, so long and short
-// requests, AES-128 and AES-256, spread over all SMs (work stealing).  The
-// round keys of the claimed tile's request are staged in shared memory; the
-// cipher is the same T-table round code as the single-buffer kernel.
+// tiles of tile_blocks / 256 whole counter groups (a counter group is 256
+// blocks sharing the counter's upper 15 bytes, the unit of counter-mode
+// caching).  A host-built table maps each tile to its request; the warps of
+// the persistent CTAs (one per SM, T-tables filled once per CTA) each claim
+// tiles through one device atomic counter until none are left, so long and
+// short requests, AES-128 and AES-256, spread over all SMs (work stealing)
+// without any CTA-wide barrier per tile.  The round keys of a warp's current
+// tile are staged in that warp's slice of shared memory; the cipher is the
+// same T-table round code as the single-buffer kernel.
 //
 // A nonzero `order` enables a test aid: tile t is processed as tile
 // (a*t + b) mod T for a host-chosen a coprime to T (a permutation), so tiles
@@ -35,40 +38,39 @@ template <int NB>
 __global__ void __launch_bounds__(1024, 1)
     batch_ttable_kernel(const BatchReq *__restrict__ reqs, const uint32_t *__restrict__ tile_req,
                         uint64_t total_tiles, unsigned long long *__restrict__ counter,
-                        const uint32_t *__restrict__ te0, uint32_t tile_blocks, TileOrder order)
+                        const uint32_t *__restrict__ te0, uint32_t tile_groups, TileOrder order)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint4 s_rk[15];
-    __shared__ unsigned long long s_tile;
-    __shared__ uint32_t s_req;
+    __shared__ uint4 s_rk[32][15];  // round keys of each warp's current tile
     aestt::fill_tables(smem, te0);
+    __syncthreads();
     const aestt::Lanes ln;
+    const uint32_t lane = threadIdx.x & 31u;
+    uint4 *w_rk = s_rk[threadIdx.x >> 5];
+    const bool permuted = order.a != 1 || order.b != 0;
+    // Every warp claims tiles on its own: no CTA-wide barrier per tile.
     for (;;) {
-        if (threadIdx.x == 0) {
-            unsigned long long t = atomicAdd(counter, 1ull);
-            if (t < total_tiles) {
-                t = (order.a * t + order.b) % total_tiles;
-                s_req = __ldg(tile_req + t);
-            }
-            s_tile = t;
-        }
-        __syncthreads();  // also publishes the tables on the first pass
-        const unsigned long long t = s_tile;
+        unsigned long long t = 0;
+        if (lane == 0)
+            t = atomicAdd(counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= total_tiles)
             break;
-        const BatchReq rq = reqs[s_req];
-        if (threadIdx.x <= rq.nr)
-            s_rk[threadIdx.x] = rq.rk[threadIdx.x];
-        __syncthreads();
-        const uint64_t nblocks = (rq.len + 15) >> 4;
-        const uint64_t first = (t - rq.tile_begin) * tile_blocks;
-        const uint64_t last = min(first + tile_blocks, nblocks);
+        if (permuted)
+            t = (order.a * t + order.b) % total_tiles;
+        const BatchReq rq = reqs[__ldg(tile_req + t)];
+        if (lane <= rq.nr)
+            w_rk[lane] = rq.rk[lane];
+        __syncwarp();
+        uint64_t first, last;
+        aestile::tile_blocks_of(t - rq.tile_begin, tile_groups, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first,
+                                &last);
         switch (rq.nr) {
-        case 10: aestile::run_tile<10, NB>(rq, first, last, smem, ln, s_rk); break;
-        case 12: aestile::run_tile<12, NB>(rq, first, last, smem, ln, s_rk); break;
-        default: aestile::run_tile<14, NB>(rq, first, last, smem, ln, s_rk); break;
+        case 10: aestile::run_tile_warp<10, NB>(rq, first, last, smem, ln, w_rk); break;
+        case 12: aestile::run_tile_warp<12, NB>(rq, first, last, smem, ln, w_rk); break;
+        default: aestile::run_tile_warp<14, NB>(rq, first, last, smem, ln, w_rk); break;
         }
-        __syncthreads();  // s_rk / s_tile are rewritten by the next claim
+        __syncwarp();  // w_rk is rewritten by the next claim
     }
 }
 
@@ -80,12 +82,8 @@ constexpr size_t kBatchSmem = aestt::kTableBytes;
 
 cudaError_t batch_set_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_ttable_kernel<1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
-    if (!e)
-        e = cudaFuncSetAttribute(batch_ttable_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kBatchSmem);
-    return e;
+    return cudaFuncSetAttribute(batch_ttable_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kBatchSmem);
 }
 
 
@@ -131,7 +129,7 @@ static int validate_batch_shape(BatchShape &s)
 {
     if (s.threads < 32 || s.threads > 1024 || (s.threads & 31))
         return AES_EINVAL;
-    if (s.tile_blocks < s.threads || s.tile_blocks % s.threads || s.tile_blocks > (1 << 22))
+    if (s.tile_blocks < 256 || s.tile_blocks % 256 || s.tile_blocks > (1 << 22))
         return AES_EINVAL;
     if (s.ctas < 0)
         return AES_EINVAL;
@@ -152,6 +150,17 @@ static BatchShape pick_batch_shape(const DeviceState &st, const aes_batch_opts_t
             s.variant = opts->variant;
     }
     return s;
+}
+
+// Tiles of a request: whole counter groups, tile_blocks / 256 per tile.
+static uint64_t tiles_of(uint64_t len, uint32_t iv_low_byte, int tile_blocks)
+{
+    const uint64_t nb = (len + 15) / 16;
+    if (!nb)
+        return 0;
+    const uint64_t groups = ((iv_low_byte + nb - 1) >> 8) + 1;
+    const uint64_t per = (uint64_t)tile_blocks / 256u;
+    return (groups + per - 1) / per;
 }
 
 static int build_tables(const aes_desc_t *descs, int n, int dev, const BatchShape &s, BatchTables &bt)
@@ -179,8 +188,7 @@ static int build_tables(const aes_desc_t *descs, int n, int dev, const BatchShap
                 return rc;
             r.in = static_cast<const uint4 *>(din);
             r.out = static_cast<uint4 *>(dout);
-            const uint64_t nb = (d.len + 15) / 16;
-            tiles += (nb + (uint64_t)s.tile_blocks - 1) / (uint64_t)s.tile_blocks;
+            tiles += tiles_of(d.len, d.iv[15], s.tile_blocks);
             bt.bytes += (int64_t)d.len;
         }
     }
@@ -190,8 +198,7 @@ static int build_tables(const aes_desc_t *descs, int n, int dev, const BatchShap
     bt.tile_req.resize((size_t)tiles);
     for (int i = 0; i < n; ++i) {
         const BatchReq &r = bt.reqs[(size_t)i];
-        const uint64_t nb = (r.len + 15) / 16;
-        const uint64_t k = (nb + (uint64_t)s.tile_blocks - 1) / (uint64_t)s.tile_blocks;
+        const uint64_t k = r.len ? tiles_of(r.len, (uint32_t)(r.iv_lo & 255u), s.tile_blocks) : 0;
         for (uint64_t t = 0; t < k; ++t)
             bt.tile_req[(size_t)(r.tile_begin + t)] = (uint32_t)i;
     }
@@ -227,13 +234,9 @@ cudaError_t launch_batch_image(uint8_t *img, const DeviceImage &im, const BatchT
     const BatchReq *reqs = reinterpret_cast<const BatchReq *>(img);
     const uint32_t *map = reinterpret_cast<const uint32_t *>(img + im.off_map);
     unsigned long long *counter = reinterpret_cast<unsigned long long *>(img + im.off_counter);
-    const uint32_t tb = (uint32_t)s.tile_blocks;
-    if (s.tile_blocks / s.threads >= 2)
-        batch_ttable_kernel<2><<<ctas, s.threads, kBatchSmem, stream>>>(reqs, map, bt.total_tiles,
-                                                                         counter, te0, tb, order);
-    else
-        batch_ttable_kernel<1><<<ctas, s.threads, kBatchSmem, stream>>>(reqs, map, bt.total_tiles,
-                                                                         counter, te0, tb, order);
+    const uint32_t tg = (uint32_t)(s.tile_blocks / 256);
+    batch_ttable_kernel<2><<<ctas, s.threads, kBatchSmem, stream>>>(reqs, map, bt.total_tiles, counter, te0,
+                                                                     tg, order);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,11 @@
 // ctr.cu -- single-buffer AES-CTR kernels (SP 800-38A Sec. 6.5).
 //
 // Two variants of the block cipher, same contract:
-//   T-table  : each warp owns 32*NB consecutive 16-byte blocks per pass (lane l
-//              takes blocks base + 32b + l, so every load/store instruction of
-//              the warp moves 512 contiguous bytes); rounds from T-tables in
-//              bank-replicated shared memory (aes_ttable.cuh).  128 KiB of
+//   T-table  : each warp owns whole 256-block counter groups (lane l takes the
+//              blocks whose counter low byte is l + 32m, so every load/store
+//              instruction of the warp moves 512 contiguous bytes); rounds from
+//              T-tables in bank-replicated shared memory with counter-mode
+//              caching of rounds 1-2 (aes_ttable.cuh, tile.cuh).  128 KiB of
 //              shared memory, one CTA per SM.
 //   bitsliced: each warp owns 1024 consecutive blocks; lane l holds blocks
 //              base + l + 32k (k = 0..31) as 128 bit planes (aes_bitslice.cuh),
@@ -16,6 +17,7 @@
 #include "common.cuh"
 #include "aes_ttable.cuh"
 #include "aes_bitslice.cuh"
+#include "tile.cuh"
 
 namespace {
 
@@ -29,36 +31,11 @@ __global__ void __launch_bounds__(1024, 1) ctr_ttable_kernel(const __grid_consta
     __syncthreads();
     const aestt::Lanes ln;
     const aestt::RkConst rk{p.rk};
-    const uint64_t nfull = p.len >> 4;
-    const uint32_t tail = (uint32_t)(p.len & 15);
-    const uint64_t nblocks = nfull + (tail ? 1 : 0);
-    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t nblocks = (p.len + 15) >> 4;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    constexpr uint64_t CH = 32 * NB;
-    for (uint64_t base = gwarp * CH; base < nblocks; base += nwarps * CH) {
-        uint32_t s[NB][4];
-        uint4 pt[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const uint64_t j = base + 32 * b + lane;
-            aesdev::counter_block(p.iv_hi, p.iv_lo, j, s[b]);
-            pt[b] = j < nfull ? aesdev::ld_stream(p.in + j) : make_uint4(0, 0, 0, 0);
-        }
-        aestt::encrypt<NR, NB>(s, smem, ln, rk);
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const uint64_t j = base + 32 * b + lane;
-            if (j < nfull) {
-                aesdev::st_stream(p.out + j, make_uint4(pt[b].x ^ s[b][0], pt[b].y ^ s[b][1],
-                                                        pt[b].z ^ s[b][2], pt[b].w ^ s[b][3]));
-            } else if (j == nfull && tail) {
-                aesdev::xor_tail(reinterpret_cast<const uint8_t *>(p.in + j),
-                                 reinterpret_cast<uint8_t *>(p.out + j), s[b][0], s[b][1], s[b][2],
-                                 s[b][3], tail);
-            }
-        }
-    }
+    aestile::xor_range<NR, NB>(p.in, p.out, p.len, p.iv_hi, p.iv_lo, 0, nblocks, gwarp, nwarps, p.parts, smem,
+                               ln, rk);
 }
 
 // Bit-plane masks of the round keys: mask[r*128 + P] = all-ones iff bit P of
@@ -189,23 +166,38 @@ int ctr_max_ctas(const CtrShape &s, int nsm)
     return nsm;
 }
 
-int ctr_ctas_for(uint64_t nblocks, const CtrShape &s, int nsm)
+void ctr_plan(uint64_t nblocks, uint32_t v0, const CtrShape &s, int nsm, int *ctas, uint32_t *parts)
 {
-    const uint64_t per_cta = (s.variant == 2) ? (uint64_t)(s.threads / 32) * 1024
-                                              : (uint64_t)s.threads * (uint64_t)s.nb;
-    uint64_t want = (nblocks + per_cta - 1) / per_cta;
     const uint64_t cap = (uint64_t)ctr_max_ctas(s, nsm);
+    const uint64_t warps = (uint64_t)(s.threads / 32);
+    uint64_t units;
+    uint32_t pt = 1;
+    if (s.variant == 2) {
+        units = (nblocks + 1023) / 1024;  // a bitsliced warp takes 1024 blocks per pass
+    } else {
+        // A T-table warp takes a whole 256-block counter group, or a part of
+        // one when the message is too short to give every warp of the
+        // largest grid a group (keeping at least NB blocks per lane per part).
+        const uint64_t groups = nblocks ? ((v0 + nblocks - 1) >> 8) + 1 : 1;
+        while (pt < 8u / (uint32_t)s.nb && groups * pt < cap * warps)
+            pt *= 2;
+        units = groups * pt;
+    }
+    uint64_t want = (units + warps - 1) / warps;
     if (s.ctas > 0)
         want = (uint64_t)s.ctas;
     if (want > cap)
         want = cap;
-    return want < 1 ? 1 : (int)want;
+    *ctas = want < 1 ? 1 : (int)want;
+    *parts = pt;
 }
 
 cudaError_t launch_ctr(const CtrParams &p, int nr, const CtrShape &s, int nsm, cudaStream_t stream)
 {
     const uint64_t nblocks = (p.len + 15) / 16;
-    const int ctas = ctr_ctas_for(nblocks, s, nsm);
+    int ctas = 1;
+    uint32_t parts = 1;
+    ctr_plan(nblocks, (uint32_t)(p.iv_lo & 255u), s, nsm, &ctas, &parts);
     if (s.variant == 2) {
         if (s.threads != 128)
             return cudaErrorInvalidValue;
@@ -217,10 +209,12 @@ cudaError_t launch_ctr(const CtrParams &p, int nr, const CtrShape &s, int nsm, c
         }
         return cudaGetLastError();
     }
+    CtrParams q = p;
+    q.parts = parts;
     switch (nr) {
-    case 10: return launch_tt<10>(p, s, ctas, stream);
-    case 12: return launch_tt<12>(p, s, ctas, stream);
-    case 14: return launch_tt<14>(p, s, ctas, stream);
+    case 10: return launch_tt<10>(q, s, ctas, stream);
+    case 12: return launch_tt<12>(q, s, ctas, stream);
+    case 14: return launch_tt<14>(q, s, ctas, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -16,6 +16,7 @@ struct CtrParams {
     uint64_t len;           // payload bytes
     uint64_t iv_hi, iv_lo;  // initial counter block as big-endian halves
     const uint32_t *te0;    // 256-word T-table seed (device)
+    uint32_t parts;         // T-table: work units per 256-block counter group (1, 2, 4, 8)
     uint32_t rk[kMaxRoundKeyWords];  // round keys, little-endian column words
 };
 
@@ -34,7 +35,9 @@ cudaError_t launch_key_expand(const uint8_t *keys, const int32_t *bits, const ui
 // Single-buffer CTR (ctr.cu).
 cudaError_t ctr_set_attributes();  // once per device
 int ctr_max_ctas(const CtrShape &s, int nsm);
-int ctr_ctas_for(uint64_t nblocks, const CtrShape &s, int nsm);
+// Grid size and counter-group split of one launch of `nblocks` blocks whose
+// initial counter has low byte v0.
+void ctr_plan(uint64_t nblocks, uint32_t v0, const CtrShape &s, int nsm, int *ctas, uint32_t *parts);
 cudaError_t launch_ctr(const CtrParams &p, int nr, const CtrShape &s, int nsm, cudaStream_t stream);
 
 // Batched varlen CTR (batch.cu).

@@ -87,7 +87,7 @@ struct SrvParams {
     const unsigned int *stop;   // mapped
     unsigned int *kstatus;      // mapped
     const uint32_t *te0;
-    uint32_t qmask, max_keys, tile_blocks, nslots;
+    uint32_t qmask, max_keys, tile_groups, nslots;
     uint64_t idle_ns, max_len;
 };
 
@@ -163,16 +163,19 @@ __device__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_wor
     if (ok && len)
         ok = in && out && !((in | out) & 15u);
     uint32_t ntiles = 0;
+    const uint64_t iv_lo = ld_volatile64(&hd->iv_lo);
     if (ok && len) {
+        // tiles are runs of tile_groups whole 256-block counter groups
         const uint64_t nb = (len + 15) >> 4;
-        ntiles = (uint32_t)((nb + p.tile_blocks - 1) / p.tile_blocks);
+        const uint64_t groups = (((iv_lo & 255u) + nb - 1) >> 8) + 1;
+        ntiles = (uint32_t)((groups + p.tile_groups - 1) / p.tile_groups);
     }
     SrvRec *rec = p.recs + d;
     rec->rq.in = reinterpret_cast<const uint4 *>(in);
     rec->rq.out = reinterpret_cast<uint4 *>(out);
     rec->rq.len = len;
     rec->rq.iv_hi = ld_volatile64(&hd->iv_hi);
-    rec->rq.iv_lo = ld_volatile64(&hd->iv_lo);
+    rec->rq.iv_lo = iv_lo;
     rec->rq.rk = p.keys + 15u * (ok ? ks : 0u);
     rec->rq.nr = (uint32_t)nr;
     rec->gen = gen;
@@ -239,30 +242,31 @@ __device__ uint32_t acquire(const SrvParams &p, uint64_t &last_work, uint32_t *d
     }
 }
 
-__global__ void __launch_bounds__(1024, 1) server_kernel(const __grid_constant__ SrvParams p)
+__global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ SrvParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint4 s_rk[15];
-    __shared__ int s_cmd;
-    __shared__ uint32_t s_tile;
+    __shared__ uint4 s_rk[16][15];  // round keys of each warp's current tile
     aestt::fill_tables(smem, p.te0);
+    __syncthreads();
     const aestt::Lanes ln;
-    uint64_t last_work = gtime();
+    const uint32_t lane = threadIdx.x & 31u;
+    uint4 *w_rk = s_rk[threadIdx.x >> 5];
+    uint64_t last_work = gtime();  // used by lane 0
+    // Every warp claims tiles on its own (lane 0 drives the cursor); no
+    // CTA-wide barrier is needed once the tables are filled.
     for (;;) {
-        if (threadIdx.x == 0) {
-            uint32_t d = 0, t = 0;
-            const uint32_t r = acquire(p, last_work, &d, &t);
-            s_cmd = r ? -(int)r : (int)d;
-            s_tile = t;
-        }
-        __syncthreads();
-        const int cmd = s_cmd;
-        if (cmd < 0) {
-            if (threadIdx.x == 0)
-                atomicOr_system(p.kstatus, (unsigned int)(-cmd));
+        uint32_t r = 0, d = 0, t = 0;
+        if (lane == 0)
+            r = acquire(p, last_work, &d, &t);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        d = __shfl_sync(0xffffffffu, d, 0);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (r) {
+            if (lane == 0)
+                atomicOr_system(p.kstatus, r);
             break;
         }
-        SrvRec *rec = p.recs + cmd;
+        SrvRec *rec = p.recs + d;
         aesrt::BatchReq rq;
         {
             const uint4 *src = reinterpret_cast<const uint4 *>(&rec->rq);
@@ -271,27 +275,26 @@ __global__ void __launch_bounds__(1024, 1) server_kernel(const __grid_constant__
             for (int i = 0; i < 4; ++i)
                 dst[i] = __ldcg(src + i);
         }
-        if (threadIdx.x <= rq.nr)
-            s_rk[threadIdx.x] = __ldcg(rq.rk + threadIdx.x);
-        __syncthreads();
-        const uint64_t nblocks = (rq.len + 15) >> 4;
-        const uint64_t first = (uint64_t)s_tile * p.tile_blocks;
-        const uint64_t last = min(first + p.tile_blocks, nblocks);
+        if (lane <= rq.nr)
+            w_rk[lane] = __ldcg(rq.rk + lane);
+        __syncwarp();
+        uint64_t first, last;
+        aestile::tile_blocks_of(t, p.tile_groups, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
         switch (rq.nr) {
-        case 10: aestile::run_tile<10, 1>(rq, first, last, smem, ln, s_rk); break;
-        case 12: aestile::run_tile<12, 1>(rq, first, last, smem, ln, s_rk); break;
-        default: aestile::run_tile<14, 1>(rq, first, last, smem, ln, s_rk); break;
+        case 10: aestile::run_tile_warp<10, 2>(rq, first, last, smem, ln, w_rk); break;
+        case 12: aestile::run_tile_warp<12, 2>(rq, first, last, smem, ln, w_rk); break;
+        default: aestile::run_tile_warp<14, 2>(rq, first, last, smem, ln, w_rk); break;
         }
-        __threadfence_system();  // this thread's output stores, before the tile is counted
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        __threadfence_system();  // this lane's output stores, before the tile is counted
+        __syncwarp();
+        if (lane == 0) {
             const uint32_t ntiles = (uint32_t)(ld_relaxed_gpu(&rec->seq_ntiles) & ((1u << kTileBits) - 1));
             const uint64_t gen = __ldcg(&rec->gen);
             __threadfence();
             const unsigned int prev = atomicAdd(&rec->done_tiles, 1u);
             if (prev + 1 == ntiles) {
                 __threadfence_system();
-                st_release_sys(p.done + cmd, (gen << 2) | 1u);
+                st_release_sys(p.done + d, (gen << 2) | 1u);
             }
             last_work = gtime();
         }
@@ -393,11 +396,11 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     const int slots = c.slots ? c.slots : 1024;
     const int max_keys = c.max_keys ? c.max_keys : 64;
     const int ctas = c.ctas ? c.ctas : std::max(1, st->nsm - 4);
-    const int threads = c.threads ? c.threads : 1024;
-    const int tile_blocks = c.tile_blocks ? c.tile_blocks : 4096;
+    const int threads = c.threads ? c.threads : 512;
+    const int tile_blocks = c.tile_blocks ? c.tile_blocks : 1024;
     if (slots < 1 || slots > kMaxSlots || max_keys < 1 || max_keys > (1 << 20) || ctas < 1 ||
-        ctas > st->nsm || threads < 32 || threads > 1024 || (threads & 31) || tile_blocks < threads ||
-        tile_blocks % threads || tile_blocks > (1 << 22))
+        ctas > st->nsm || threads < 32 || threads > 512 || (threads & 31) || tile_blocks < 256 ||
+        tile_blocks % 256 || tile_blocks > (1 << 22))
         return AES_EINVAL;
     offload_server_s *s = new (std::nothrow) offload_server_s();
     if (!s)
@@ -410,7 +413,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     s->tile_blocks = tile_blocks;
     s->budget = c.hbm_budget;
     s->idle_ns = 1000ull * (c.idle_timeout_us ? c.idle_timeout_us : 200000u);
-    s->max_len = std::min<uint64_t>(16ull << 30, (uint64_t)kMaxTiles * (uint64_t)tile_blocks * 16u);
+    s->max_len = std::min<uint64_t>(16ull << 30, ((uint64_t)kMaxTiles - 1) * (uint64_t)tile_blocks * 16u);
     uint32_t q = 1;
     while (q < (uint32_t)slots)
         q <<= 1;
@@ -488,7 +491,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     P.te0 = st->te0;
     P.qmask = q - 1;
     P.max_keys = (uint32_t)max_keys;
-    P.tile_blocks = (uint32_t)tile_blocks;
+    P.tile_groups = (uint32_t)(tile_blocks / 256);
     P.nslots = (uint32_t)slots;
     P.idle_ns = s->idle_ns;
     P.max_len = s->max_len;

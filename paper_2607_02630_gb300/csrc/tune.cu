@@ -57,7 +57,7 @@ void tune_defaults(DeviceState &st)
     for (int i = 0; i < 3; ++i)
         for (int b = 0; b < kLenBuckets; ++b)
             st.ctr_tuned[i][b] = default_shape(st.nsm, b);
-    st.batch_tuned = BatchShape{AES_VARIANT_TTABLE, 1024, 8192, 0};
+    st.batch_tuned = BatchShape{AES_VARIANT_TTABLE, 1024, 1024, 0};
 }
 
 CtrShape tuned_ctr_shape(const DeviceState &st, size_t len, int nr)
@@ -108,7 +108,8 @@ int aes_tuned_shape(size_t len, int bits, aes_launch_t *out)
     out->variant = s.variant;
     out->threads = s.threads;
     out->blocks_per_thread = s.nb;
-    out->ctas = ctr_ctas_for((len + 15) / 16, s, st->nsm);
+    uint32_t parts = 1;
+    ctr_plan((len + 15) / 16, 0, s, st->nsm, &out->ctas, &parts);
     return AES_OK;
 }
 
