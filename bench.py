@@ -225,6 +225,241 @@ def reference_arm(args, ws, rank):
     return 0
 
 
+def sweep(args, rank, local):
+    """Single-buffer sweep: for every size, key size and cipher variant the
+    median of --sweep-reps aes_ctr launches (CUDA events on the launch
+    stream), counter low word starting at 2^32 - 8.  Buffers rotate through
+    a pool, and L2 is flushed (a write of twice its size) before every timed
+    launch, so every launch reads its input from HBM."""
+    import torch
+
+    from paper_2607_02630_gb300 import aesoffload as A
+    from paper_2607_02630_gb300 import build as libbuild
+
+    torch.cuda.set_device(local)
+    libbuild.build()
+    A.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = int(stream.cuda_stream)
+    props = torch.cuda.get_device_properties(dev)
+    nsm, l2 = props.multi_processor_count, props.L2_cache_size
+    pk, pk_kind = peaks()
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    sizes = [int(x) for x in args.sweep_sizes.split(",")]
+    bits_list = [int(x) for x in args.sweep_bits.split(",")]
+    variants = {"ttable": dict(variant=1, threads=512, blocks_per_thread=1),
+                "bitslice": dict(variant=2, threads=128), "auto": {}}
+    chosen = [v for v in args.sweep_variants.split(",")]
+    pool_bytes = max(2 * l2 + (64 << 20), max(sizes))
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
+    rows = []
+    with ClockSampler(local) as clk:
+        for n in sizes:
+            nbuf = min(max(1, -(-pool_bytes // n)), args.sweep_reps + 3)
+            src = torch.empty(nbuf * n, dtype=torch.uint8, device=dev).random_(0, 256)
+            dst = torch.empty_like(src)
+            for bits in bits_list:
+                w = W.single_buffer(16, bits, seed=W.SEED_BASE + 2, low32=0xFFFFFFF8)
+                ctx = A.Context(w.key.tobytes(), bits)
+                iv = w.iv.tobytes()
+                nblocks = (n + 15) // 16
+                nr = bits // 32 + 6
+                for name in chosen:
+                    shape = variants[name]
+                    for k in range(3):
+                        A.ctr(ctx, iv, src.data_ptr() + (k % nbuf) * n, dst.data_ptr() + (k % nbuf) * n, n,
+                              stream=sh, **shape)
+                    times = []
+                    for k in range(args.sweep_reps):
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        o = (k % nbuf) * n
+                        with torch.cuda.stream(stream):
+                            flush.fill_(k & 255)
+                        a.record(stream)
+                        A.ctr(ctx, iv, src.data_ptr() + o, dst.data_ptr() + o, n, stream=sh, **shape)
+                        b.record(stream)
+                        stream.synchronize()
+                        times.append(a.elapsed_time(b) / 1e3)
+                    t = statistics.median(times)
+                    gbs = n / t / 1e9
+                    if name == "bitslice":
+                        # ALU-bound: logic ops at 64 lanes/clk/SM; floor per 32 blocks:
+                        # 16 Boyar-Peralta S-boxes (113 gates) per round, MixColumns
+                        # (416 xors) per full round, AddRoundKey (128 xors) per key
+                        ops = (16 * 113 * nr + 416 * (nr - 1) + 128 * (nr + 1)) / 32.0
+                        roof = nsm * mhz * 1e6 * 64.0 / ops * 16 / 1e9
+                        bound = "alu (LOP3, 64/clk/SM)"
+                    else:
+                        groups = ((255 + nblocks - 1) >> 8) + 1
+                        lookups = nblocks * (16 * nr - 27) + 27 * groups
+                        roof = n / (lookups / (32.0 * nsm * mhz * 1e6)) / 1e9
+                        bound = "shared-memory wavefronts (32 lookups/clk/SM)"
+                    rows.append({"bytes": n, "bits": bits, "variant": name, "us": round(t * 1e6, 3),
+                                 "gbs": round(gbs, 2), "roofline_gbs": round(min(roof, float(pk.get("hbm_gbs", 6784.5)) / 2), 1),
+                                 "frac": round(gbs / min(roof, float(pk.get("hbm_gbs", 6784.5)) / 2), 4),
+                                 "bound": bound,
+                                 "hbm_gbs_moved": round(2 * n / t / 1e9, 1)})
+                ctx.close()
+            del src, dst
+            torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"metric": "AES-CTR single-buffer sweep GB/s (% roofline)", "unit": UNIT,
+                          "l2_bytes": l2, "peak_kind": pk_kind, "sm_max_mhz": mhz,
+                          "clocks": clk.summary(), "rows": rows}), flush=True)
+    return 0
+
+
+def _pct(x, q):
+    x = [v for v in x if v >= 0]
+    return round(float(np.percentile(x, q)), 2) if x else None
+
+
+def served(args, rank, local):
+    """Served-mode studies through the native open-loop drivers.
+
+    Open loop: the saturated request rate R_sat of the served path is
+    measured first (all arrivals at t = 0); then Poisson arrivals at 0.2, 0.4,
+    0.6, 0.8 and 1.0 x R_sat, split over 8 submitter threads, for the served
+    path and, on the same schedule, for per-call aes_ctr launches polled with
+    cudaEventQuery.  Sizes: 70% 1 MiB, 10% 8 MiB, 20% log-uniform 4-64 KiB;
+    64 resident keys (AES-128/256 50/50), one drawn per request.
+    Stream: AES-256, 2048 x 8 MiB (16 GiB), at most 512 in flight, an HBM
+    budget of 20 GiB and then 2 GiB (back-pressure), a new random key every
+    1024 requests; sustained GB/s, p50/p99, and oracle spot checks (every
+    64th request in full, four 4 KiB windows of every request)."""
+    import torch
+
+    import oracle
+    from paper_2607_02630_gb300 import aesoffload as A
+    from paper_2607_02630_gb300 import build as libbuild
+
+    torch.cuda.set_device(local)
+    libbuild.build()
+    A.lib()
+    dev = torch.device("cuda", local)
+    MiB = 1 << 20
+    out = {"metric": "served AES-CTR: open-loop p50/p99 and GB/s vs per-call; 8 MiB stream", "unit": UNIT}
+
+    # ---------------- open loop
+    n = args.served_requests
+    sizes = W.served_sizes(n, seed=W.SEED_BASE + 4)
+    kbits, kbytes = W.key_set(64, seed=W.SEED_BASE + 5)
+    g = W.rng(W.SEED_BASE + 6)
+    key_idx = g.integers(0, 64, n)
+    ivs = W.random_bytes(g, 16 * n).reshape(n, 16)
+    pool_n, ring_n = 64, 2048
+    gen = torch.Generator(device=dev).manual_seed(W.SEED_BASE + 4)
+    pool = torch.randint(0, 256, (pool_n * 8 * MiB,), dtype=torch.uint8, device=dev, generator=gen)
+    ring = torch.empty(ring_n * 8 * MiB, dtype=torch.uint8, device=dev)
+    ctxs = [A.Context(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)]
+    srv = A.Server(slots=1024, max_keys=64, idle_timeout_us=2_000_000)
+    slots = [srv.key_register(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)]
+    reqs = np.zeros(n, dtype=A.drive_dtype())
+    reqs["iv"] = ivs
+    reqs["inp"] = pool.data_ptr() + (np.arange(n) % pool_n) * 8 * MiB
+    reqs["out"] = ring.data_ptr() + (np.arange(n) % ring_n) * 8 * MiB
+    reqs["len"] = sizes
+    served_reqs = reqs.copy()
+    served_reqs["key_slot"] = np.array(slots)[key_idx]
+    pc_reqs = reqs.copy()
+    pc_reqs["key_slot"] = key_idx
+    total = int(sizes.sum())
+    one_mib = sizes == MiB
+    lat, res = A.drive_served(srv, served_reqs, 8)  # warm-up (also relaunch, key pages)
+    lat, res = A.drive_served(srv, served_reqs, 8)
+    r_sat = n / res["elapsed_s"]
+    sat = {"req_per_s": round(r_sat, 1), "gbs": round(total / res["elapsed_s"] / 1e9, 2),
+           "p50_us": _pct(lat, 50), "p99_us": _pct(lat, 99), "errors": res["errors"]}
+    lat_pc, res_pc = A.drive_per_call(ctxs, pc_reqs, 8)
+    sat_pc = {"req_per_s": round(n / res_pc["elapsed_s"], 1), "gbs": round(total / res_pc["elapsed_s"] / 1e9, 2),
+              "errors": res_pc["errors"]}
+    rates = []
+    for frac in (0.2, 0.4, 0.6, 0.8, 1.0):
+        rate = frac * r_sat
+        arr = W.poisson_arrivals(n, rate, seed=W.SEED_BASE + 40 + int(frac * 10))
+        served_reqs["arrival_s"] = arr
+        pc_reqs["arrival_s"] = arr
+        lat, res = A.drive_served(srv, served_reqs, 8)
+        lat_pc, res_pc = A.drive_per_call(ctxs, pc_reqs, 8)
+        rates.append({
+            "offered_frac_of_rsat": frac, "offered_req_per_s": round(rate, 1),
+            "served": {"p50_us": _pct(lat, 50), "p99_us": _pct(lat, 99),
+                       "p50_1mib_us": _pct(lat[one_mib], 50), "p99_1mib_us": _pct(lat[one_mib], 99),
+                       "gbs": round(res["bytes"] / res["elapsed_s"] / 1e9, 2), "errors": res["errors"],
+                       "eagain_retries": res["eagain_retries"]},
+            "per_call": {"p50_us": _pct(lat_pc, 50), "p99_us": _pct(lat_pc, 99),
+                         "p50_1mib_us": _pct(lat_pc[one_mib], 50), "p99_1mib_us": _pct(lat_pc[one_mib], 99),
+                         "gbs": round(res_pc["bytes"] / res_pc["elapsed_s"] / 1e9, 2), "errors": res_pc["errors"]}})
+    srv.close()
+    out["open_loop"] = {"requests_per_rate": n, "payload_bytes_per_rate": total, "submitter_threads": 8,
+                        "saturation_served": sat, "saturation_per_call": sat_pc, "rates": rates}
+    del pool, ring, ctxs
+    torch.cuda.empty_cache()
+
+    # ---------------- large stream
+    n5, big = 2048, 8 * MiB
+    gen = torch.Generator(device=dev).manual_seed(W.SEED_BASE + 5)
+    src = torch.randint(0, 256, (n5 * big,), dtype=torch.uint8, device=dev, generator=gen)
+    dst = torch.empty_like(src)
+    g = W.rng(W.SEED_BASE + 7)
+    keys5 = [W.random_bytes(g, 32) for _ in range(n5 // 1024)]
+    ivs5 = W.random_bytes(g, 16 * n5).reshape(n5, 16)
+    stream = {}
+    for budget in (20 << 30, 2 << 30):
+        srv = A.Server(slots=512, max_keys=4, hbm_budget=budget, idle_timeout_us=2_000_000)
+        ks = [srv.key_register(k.tobytes(), 256) for k in keys5]
+        r5 = np.zeros(n5, dtype=A.drive_dtype())
+        r5["key_slot"] = np.array(ks)[np.arange(n5) // 1024]
+        r5["iv"] = ivs5
+        r5["inp"] = src.data_ptr() + np.arange(n5) * big
+        r5["out"] = dst.data_ptr() + np.arange(n5) * big
+        r5["len"] = big
+        lat, res = A.drive_served(srv, r5, 8)  # closed: everything offered at t = 0
+        gbs = res["bytes"] / res["elapsed_s"] / 1e9
+        r5["arrival_s"] = np.arange(n5) / (0.9 * n5 / res["elapsed_s"])  # paced at 90% of that rate
+        lat_p, res_p = A.drive_served(srv, r5, 8)
+        stream[f"budget_{budget >> 30}GiB"] = {
+            "sustained_gbs": round(gbs, 2), "eagain_retries": res["eagain_retries"], "errors": res["errors"],
+            "paced_90pct": {"p50_us": _pct(lat_p, 50), "p99_us": _pct(lat_p, 99),
+                            "gbs": round(res_p["bytes"] / res_p["elapsed_s"] / 1e9, 2)}}
+        srv.close()
+    # spot checks against the oracle
+    nthreads = os.cpu_count() or 1
+    torch.cuda.synchronize()
+    bad, checked = 0, 0
+    gw = W.rng(W.SEED_BASE + 8)
+    for i in range(n5):
+        key, iv = keys5[i // 1024], ivs5[i]
+        base = i * big
+        spans = [(0, big)] if i % 64 == 0 else []
+        spans += [(int(o) * 16, int(o) * 16 + 4096) for o in gw.integers(0, (big - 4096) // 16, 4)]
+        for a, b in spans:
+            pin = src[base + a: base + b].cpu().numpy()
+            got = dst[base + a: base + b].cpu().numpy()
+            ivw = np.frombuffer(((int.from_bytes(iv.tobytes(), "big") + a // 16) % (1 << 128)).to_bytes(16, "big"),
+                                np.uint8)
+            want = oracle.ctr_mt(key, 256, ivw, pin, nthreads)
+            checked += b - a
+            bad += int(not np.array_equal(got, want))
+    stream["spot_check"] = {"bytes_checked": checked, "mismatched_spans": bad,
+                            "how": "every 64th request in full + four 4 KiB windows of every request vs the oracle"}
+    roof = None
+    try:
+        pk, _ = peaks()
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        lookups_per_block = 16 * 14 - 27 + 27 / 256.0
+        roof = 32.0 * nsm * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / lookups_per_block * 16 / 1e9
+    except Exception:
+        pass
+    stream["roofline_gbs_aes256"] = round(roof, 1) if roof else None
+    out["stream_8mib_aes256"] = stream
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------- our arm
 
 def main():
@@ -238,10 +473,23 @@ def main():
     ap.add_argument("--requests", type=int, default=4096,
                     help="requests per step (4096 = the benchmark workload; fewer only for profiler captures)")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--sweep", action="store_true",
+                    help="single-buffer sweep instead of the batch step: sizes x key sizes x variants")
+    ap.add_argument("--sweep-sizes", default="4096,16384,65536,262144,1048576,4194304,16777216,67108864,268435456")
+    ap.add_argument("--sweep-bits", default="128,256")
+    ap.add_argument("--sweep-variants", default="ttable,bitslice")
+    ap.add_argument("--sweep-reps", type=int, default=20)
+    ap.add_argument("--served", action="store_true",
+                    help="served-mode studies: open-loop Poisson rates and the large 8 MiB stream")
+    ap.add_argument("--served-requests", type=int, default=20000)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
+    if args.sweep:
+        return sweep(args, rank, local)
+    if args.served:
+        return served(args, rank, local)
 
     import torch
 

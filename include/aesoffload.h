@@ -222,7 +222,7 @@ typedef struct {
                                in-place counted once); 0 = unlimited */
     int ctas;               /* resident CTAs; 0 = SM count - 4 */
     int threads;            /* CTA size, multiple of 32, <= 512; 0 = 512 */
-    int tile_blocks;        /* 16-byte blocks per tile, multiple of 256; 0 = 1024 */
+    int tile_blocks;        /* 16-byte blocks per tile, multiple of 256; 0 = 256 per warp of a CTA */
     uint32_t idle_timeout_us; /* resident kernel exits after this long with no
                                  work (relaunched on the next submit); 0 = 200000 */
 } offload_cfg_t;
@@ -267,6 +267,46 @@ int offload_server_stats(offload_server_t srv, offload_stats_t *out);
  * AES_ETIMEOUT if the kernel did not exit in time (resources are then leaked
  * rather than freed under a running kernel). */
 int offload_server_destroy(offload_server_t srv);
+
+/* ------------------------------------------------------------ load drivers */
+
+/* Open-loop load drivers for the served and per-call paths.  The paper
+ * measures latency under offered load with open-loop Poisson arrivals and
+ * reports median and tail latency (Sec. 6, "Latency under offered load"),
+ * and its servers hand each offload to a pool of executor threads (Sec. 3,
+ * Listing 1).  These drivers reproduce that measurement natively:
+ * `nthreads` submitter threads, thread k owning requests k, k+nthreads, ...,
+ * each submitted at its scheduled arrival_s (seconds from the call) or as
+ * soon after as the thread can, and latency_us[i] = time from the scheduled
+ * arrival to the moment the thread observes completion (-1 on error).
+ * reqs must be sorted by arrival_s.  Host-side only; synchronous. */
+typedef struct {
+    int key_slot;       /* offload_drive: server key slot; aes_ctr_drive: index into ctxs */
+    uint8_t iv[16];
+    const void *in;
+    void *out;
+    size_t len;
+    double arrival_s;
+} aes_drive_req_t;
+
+typedef struct {
+    double elapsed_s;         /* first scheduled arrival to last completion */
+    uint64_t bytes;           /* payload bytes completed */
+    uint64_t eagain_retries;  /* submissions retried after AES_EAGAIN */
+    int errors;               /* requests that failed */
+} aes_drive_result_t;
+
+/* Served path: offload_submit, then offload_poll until AES_OK; AES_EAGAIN
+ * (back-pressure) is retried.  Errors: AES_EINVAL for bad arguments. */
+int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int nthreads,
+                  double *latency_us, aes_drive_result_t *res);
+
+/* Per-call path with the same schedule: each thread owns a CUDA stream,
+ * launches aes_ctr, records an event and polls it with cudaEventQuery (the
+ * paper's completion mechanism, Sec. 6 setup); at most 256 requests in
+ * flight per thread. */
+int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, int n, int nthreads,
+                  double *latency_us, aes_drive_result_t *res);
 
 #ifdef __cplusplus
 }

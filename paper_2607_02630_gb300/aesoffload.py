@@ -74,6 +74,11 @@ class ServerStats(ctypes.Structure):
                 ("kernel_status", ctypes.c_uint32), ("running", ctypes.c_int)]
 
 
+class DriveResult(ctypes.Structure):
+    _fields_ = [("elapsed_s", ctypes.c_double), ("bytes", ctypes.c_uint64),
+                ("eagain_retries", ctypes.c_uint64), ("errors", ctypes.c_int)]
+
+
 _SIGS = {
     "aes_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "aes_last_error": (ctypes.c_char_p, []),
@@ -106,6 +111,10 @@ _SIGS = {
     "offload_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]),
     "offload_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "offload_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "offload_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
+    "aes_ctr_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
 }
 
 
@@ -340,3 +349,42 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# aes_drive_req_t as a numpy record (C layout: int, 16 bytes, pad, 3 x 8-byte fields, double)
+def drive_dtype():
+    import numpy as np
+
+    return np.dtype({"names": ["key_slot", "iv", "inp", "out", "len", "arrival_s"],
+                     "formats": ["<i4", ("u1", 16), "<u8", "<u8", "<u8", "<f8"],
+                     "offsets": [0, 4, 24, 32, 40, 48], "itemsize": 56})
+
+
+def _drive_result(res: DriveResult) -> dict:
+    return {"elapsed_s": res.elapsed_s, "bytes": res.bytes, "eagain_retries": res.eagain_retries,
+            "errors": res.errors}
+
+
+def drive_served(server: "Server", reqs, nthreads: int = 8):
+    """offload_drive over a drive_dtype() array; returns (latency_us array, result dict)."""
+    import numpy as np
+
+    reqs = np.ascontiguousarray(reqs, dtype=drive_dtype())
+    lat = np.zeros(len(reqs), np.float64)
+    res = DriveResult()
+    _check(lib().offload_drive(server.handle, reqs.ctypes.data, len(reqs), int(nthreads), lat.ctypes.data,
+                               ctypes.byref(res)), "offload_drive")
+    return lat, _drive_result(res)
+
+
+def drive_per_call(ctxs, reqs, nthreads: int = 8):
+    """aes_ctr_drive with key_slot indexing `ctxs`; returns (latency_us array, result dict)."""
+    import numpy as np
+
+    reqs = np.ascontiguousarray(reqs, dtype=drive_dtype())
+    handles = (ctypes.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+    lat = np.zeros(len(reqs), np.float64)
+    res = DriveResult()
+    _check(lib().aes_ctr_drive(handles, len(ctxs), reqs.ctypes.data, len(reqs), int(nthreads),
+                               lat.ctypes.data, ctypes.byref(res)), "aes_ctr_drive")
+    return lat, _drive_result(res)

@@ -79,7 +79,7 @@ int device_state_ready(DeviceState **out)
 
 // A payload pointer must be device-addressable on `dev`: device or managed
 // memory of that device, or pinned host memory (its device alias is used).
-int resolve_ptr(const void *p, int dev, const void **dptr)
+int resolve_ptr(const void *p, int dev, const void **dptr, bool *is_host)
 {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -98,13 +98,16 @@ int resolve_ptr(const void *p, int dev, const void **dptr)
         if (!a.devicePointer)
             return AES_EPTR;
         *dptr = a.devicePointer;
+        if (is_host)
+            *is_host = true;
         return AES_OK;
     default:
         return AES_EPTR;
     }
 }
 
-int check_payload(const void *in, const void *out, size_t len, int dev, const void **din, void **dout)
+int check_payload(const void *in, const void *out, size_t len, int dev, const void **din, void **dout,
+                  bool *out_is_host)
 {
     if (!in || !out)
         return AES_EINVAL;
@@ -116,14 +119,18 @@ int check_payload(const void *in, const void *out, size_t len, int dev, const vo
             return AES_EOVERLAP;
     }
     const void *di = nullptr, *dout_c = nullptr;
-    int rc = resolve_ptr(in, dev, &di);
+    bool in_host = false, o_host = false;
+    int rc = resolve_ptr(in, dev, &di, &in_host);
     if (rc)
         return rc;
     if (out == in) {
         dout_c = di;
-    } else if ((rc = resolve_ptr(out, dev, &dout_c))) {
+        o_host = in_host;
+    } else if ((rc = resolve_ptr(out, dev, &dout_c, &o_host))) {
         return rc;
     }
+    if (out_is_host)
+        *out_is_host = o_host;
     *din = di;
     *dout = const_cast<void *>(dout_c);
     return AES_OK;

@@ -1,0 +1,195 @@
+// harness.cu -- open-loop drivers for the served and per-call paths.
+//
+// The paper measures latency under offered load with open-loop Poisson
+// arrivals and reports median and tail latency (Sec. 6, "Latency under
+// offered load"), and its servers hand offloads to a pool of executor
+// threads (Sec. 3, Listing 1).  These drivers reproduce that measurement on
+// the library's own entry points: `nthreads` submitter threads, thread k
+// owning requests k, k + nthreads, ...; each request is submitted at its
+// scheduled arrival time (never earlier; late if the thread is behind, which
+// counts against the latency, so there is no coordinated omission), and its
+// latency is the time from the scheduled arrival to the moment the thread
+// observes completion.
+#include "../../include/aesoffload.h"
+#include "internal.h"
+#include "runtime.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <thread>
+#include <vector>
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+double seconds_since(clk::time_point t0)
+{
+    return std::chrono::duration<double>(clk::now() - t0).count();
+}
+
+struct Shared {
+    std::atomic<uint64_t> bytes{0}, retries{0};
+    std::atomic<int> errors{0};
+    std::atomic<double> last_done{0.0};
+};
+
+void note_done(Shared &sh, double t)
+{
+    double cur = sh.last_done.load();
+    while (t > cur && !sh.last_done.compare_exchange_weak(cur, t)) {
+    }
+}
+
+}  // namespace
+
+using namespace aesrt;
+
+extern "C" {
+
+int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int nthreads,
+                  double *latency_us, aes_drive_result_t *res)
+{
+    if (!srv || (n > 0 && (!reqs || !latency_us)) || n < 0 || nthreads < 1 || nthreads > 256 || !res)
+        return AES_EINVAL;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Shared sh;
+    const clk::time_point t0 = clk::now();
+    auto worker = [&](int k) {
+        cudaSetDevice(dev);
+        std::vector<std::pair<uint64_t, int>> pending;  // (ticket, request index)
+        int next = k;
+        while (next < n || !pending.empty()) {
+            if (next < n && seconds_since(t0) >= reqs[next].arrival_s) {
+                const aes_drive_req_t &r = reqs[next];
+                uint64_t t = 0;
+                const int rc = offload_submit(srv, r.key_slot, r.iv, r.in, r.out, r.len, &t);
+                if (rc == AES_OK) {
+                    pending.emplace_back(t, next);
+                    next += nthreads;
+                } else if (rc == AES_EAGAIN) {
+                    sh.retries.fetch_add(1);  // back-pressure: poll below, then retry
+                } else {
+                    latency_us[next] = -1.0;
+                    sh.errors.fetch_add(1);
+                    next += nthreads;
+                }
+            }
+            for (size_t i = 0; i < pending.size();) {
+                const int rc = offload_poll(srv, pending[i].first);
+                if (rc == AES_PENDING) {
+                    ++i;
+                    continue;
+                }
+                const int idx = pending[i].second;
+                const double now = seconds_since(t0);
+                if (rc == AES_OK) {
+                    latency_us[idx] = (now - reqs[idx].arrival_s) * 1e6;
+                    sh.bytes.fetch_add(reqs[idx].len);
+                    note_done(sh, now);
+                } else {
+                    latency_us[idx] = -1.0;
+                    sh.errors.fetch_add(1);
+                }
+                pending[i] = pending.back();
+                pending.pop_back();
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int k = 0; k < nthreads; ++k)
+        th.emplace_back(worker, k);
+    for (auto &t : th)
+        t.join();
+    const double first = n ? reqs[0].arrival_s : 0.0;
+    res->elapsed_s = sh.last_done.load() - first;
+    res->bytes = sh.bytes.load();
+    res->eagain_retries = sh.retries.load();
+    res->errors = sh.errors.load();
+    return AES_OK;
+}
+
+int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, int n, int nthreads,
+                  double *latency_us, aes_drive_result_t *res)
+{
+    if (!ctxs || nctx < 1 || (n > 0 && (!reqs || !latency_us)) || n < 0 || nthreads < 1 || nthreads > 256 ||
+        !res)
+        return AES_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (reqs[i].key_slot < 0 || reqs[i].key_slot >= nctx)
+            return AES_EINVAL;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Shared sh;
+    const clk::time_point t0 = clk::now();
+    auto worker = [&](int k) {
+        cudaSetDevice(dev);
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            sh.errors.fetch_add(1);
+            return;
+        }
+        constexpr int kMaxPending = 256;
+        std::vector<cudaEvent_t> free_ev;
+        for (int i = 0; i < kMaxPending; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess)
+                free_ev.push_back(e);
+        }
+        std::vector<std::pair<cudaEvent_t, int>> pending;
+        int next = k;
+        while (next < n || !pending.empty()) {
+            if (next < n && !free_ev.empty() && seconds_since(t0) >= reqs[next].arrival_s) {
+                const aes_drive_req_t &r = reqs[next];
+                const int rc = aes_ctr(ctxs[r.key_slot], r.iv, r.in, r.out, r.len, s);
+                cudaEvent_t e = free_ev.back();
+                if (rc == AES_OK && cudaEventRecord(e, s) == cudaSuccess) {
+                    free_ev.pop_back();
+                    pending.emplace_back(e, next);
+                } else {
+                    latency_us[next] = -1.0;
+                    sh.errors.fetch_add(1);
+                }
+                next += nthreads;
+            }
+            for (size_t i = 0; i < pending.size();) {
+                const cudaError_t q = cudaEventQuery(pending[i].first);
+                if (q == cudaErrorNotReady) {
+                    ++i;
+                    continue;
+                }
+                const int idx = pending[i].second;
+                const double now = seconds_since(t0);
+                if (q == cudaSuccess) {
+                    latency_us[idx] = (now - reqs[idx].arrival_s) * 1e6;
+                    sh.bytes.fetch_add(reqs[idx].len);
+                    note_done(sh, now);
+                } else {
+                    latency_us[idx] = -1.0;
+                    sh.errors.fetch_add(1);
+                }
+                free_ev.push_back(pending[i].first);
+                pending[i] = pending.back();
+                pending.pop_back();
+            }
+        }
+        for (cudaEvent_t e : free_ev)
+            cudaEventDestroy(e);
+        cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> th;
+    for (int k = 0; k < nthreads; ++k)
+        th.emplace_back(worker, k);
+    for (auto &t : th)
+        t.join();
+    const double first = n ? reqs[0].arrival_s : 0.0;
+    res->elapsed_s = sh.last_done.load() - first;
+    res->bytes = sh.bytes.load();
+    res->eagain_retries = 0;
+    res->errors = sh.errors.load();
+    return AES_OK;
+}
+
+}  // extern "C"

@@ -34,8 +34,11 @@ extern thread_local char g_last_error[256];
 int cuda_fail(cudaError_t e, const char *where);
 int device_state(DeviceState **out);
 int device_state_ready(DeviceState **out);
-int resolve_ptr(const void *p, int dev, const void **dptr);
-int check_payload(const void *in, const void *out, size_t len, int dev, const void **din, void **dout);
+// A payload pointer the GPU can address on `dev`: device or managed memory of
+// that device, or pinned host memory (*is_host set); its device alias in *dptr.
+int resolve_ptr(const void *p, int dev, const void **dptr, bool *is_host = nullptr);
+int check_payload(const void *in, const void *out, size_t len, int dev, const void **din, void **dout,
+                  bool *out_is_host = nullptr);
 void iv_halves(const uint8_t *iv, uint64_t *hi, uint64_t *lo);
 
 // tune.cu

@@ -55,7 +55,7 @@ constexpr uint32_t kExitStop = 1, kExitIdle = 2, kExitError = 4;
 
 struct HostDesc {  // 64 bytes, host-written
     uint64_t in, out, len, iv_hi, iv_lo, gen;
-    uint32_t key_slot, pad0;
+    uint32_t key_slot, flags;  // flags bit 0: the output is pinned host memory
     uint64_t pad1;
 };
 static_assert(sizeof(HostDesc) == 64, "HostDesc layout");
@@ -178,6 +178,7 @@ __device__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_wor
     rec->rq.iv_lo = iv_lo;
     rec->rq.rk = p.keys + 15u * (ok ? ks : 0u);
     rec->rq.nr = (uint32_t)nr;
+    rec->rq.pad = ld_volatile(&hd->flags);
     rec->gen = gen;
     rec->done_tiles = 0;
     __threadfence();
@@ -245,28 +246,30 @@ __device__ uint32_t acquire(const SrvParams &p, uint64_t &last_work, uint32_t *d
 __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ SrvParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint4 s_rk[16][15];  // round keys of each warp's current tile
+    __shared__ uint4 s_rk[15];
+    __shared__ int s_cmd;
+    __shared__ uint32_t s_tile;
     aestt::fill_tables(smem, p.te0);
-    __syncthreads();
     const aestt::Lanes ln;
-    const uint32_t lane = threadIdx.x & 31u;
-    uint4 *w_rk = s_rk[threadIdx.x >> 5];
-    uint64_t last_work = gtime();  // used by lane 0
-    // Every warp claims tiles on its own (lane 0 drives the cursor); no
-    // CTA-wide barrier is needed once the tables are filled.
+    uint64_t last_work = gtime();  // used by thread 0
+    // Thread 0 claims a tile for the whole CTA (so at most one poller per
+    // CTA touches the cursor); a tile is tile_groups counter groups, one per
+    // warp by default, so the per-tile barrier waits for no straggler.
     for (;;) {
-        uint32_t r = 0, d = 0, t = 0;
-        if (lane == 0)
-            r = acquire(p, last_work, &d, &t);
-        r = __shfl_sync(0xffffffffu, r, 0);
-        d = __shfl_sync(0xffffffffu, d, 0);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (r) {
-            if (lane == 0)
-                atomicOr_system(p.kstatus, r);
+        if (threadIdx.x == 0) {
+            uint32_t d = 0, t = 0;
+            const uint32_t r = acquire(p, last_work, &d, &t);
+            s_cmd = r ? -(int)r : (int)d;
+            s_tile = t;
+        }
+        __syncthreads();  // also publishes the tables on the first pass
+        const int cmd = s_cmd;
+        if (cmd < 0) {
+            if (threadIdx.x == 0)
+                atomicOr_system(p.kstatus, (unsigned int)(-cmd));
             break;
         }
-        SrvRec *rec = p.recs + d;
+        SrvRec *rec = p.recs + cmd;
         aesrt::BatchReq rq;
         {
             const uint4 *src = reinterpret_cast<const uint4 *>(&rec->rq);
@@ -275,26 +278,32 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
             for (int i = 0; i < 4; ++i)
                 dst[i] = __ldcg(src + i);
         }
-        if (lane <= rq.nr)
-            w_rk[lane] = __ldcg(rq.rk + lane);
-        __syncwarp();
+        if (threadIdx.x <= rq.nr)
+            s_rk[threadIdx.x] = __ldcg(rq.rk + threadIdx.x);
+        const uint32_t tile = s_tile;
+        __syncthreads();
         uint64_t first, last;
-        aestile::tile_blocks_of(t, p.tile_groups, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
+        aestile::tile_blocks_of(tile, p.tile_groups, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
         switch (rq.nr) {
-        case 10: aestile::run_tile_warp<10, 2>(rq, first, last, smem, ln, w_rk); break;
-        case 12: aestile::run_tile_warp<12, 2>(rq, first, last, smem, ln, w_rk); break;
-        default: aestile::run_tile_warp<14, 2>(rq, first, last, smem, ln, w_rk); break;
+        case 10: aestile::run_tile<10, 2>(rq, first, last, smem, ln, s_rk); break;
+        case 12: aestile::run_tile<12, 2>(rq, first, last, smem, ln, s_rk); break;
+        default: aestile::run_tile<14, 2>(rq, first, last, smem, ln, s_rk); break;
         }
-        __threadfence_system();  // this lane's output stores, before the tile is counted
-        __syncwarp();
-        if (lane == 0) {
+        // Order this thread's output stores before the tile is counted: at
+        // system scope when the output lives in host memory, else GPU scope
+        // (the completing thread's system-scope release covers the rest).
+        if (rq.pad & 1u)
+            __threadfence_system();
+        else
+            __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
             const uint32_t ntiles = (uint32_t)(ld_relaxed_gpu(&rec->seq_ntiles) & ((1u << kTileBits) - 1));
             const uint64_t gen = __ldcg(&rec->gen);
-            __threadfence();
             const unsigned int prev = atomicAdd(&rec->done_tiles, 1u);
             if (prev + 1 == ntiles) {
                 __threadfence_system();
-                st_release_sys(p.done + d, (gen << 2) | 1u);
+                st_release_sys(p.done + cmd, (gen << 2) | 1u);
             }
             last_work = gtime();
         }
@@ -397,7 +406,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     const int max_keys = c.max_keys ? c.max_keys : 64;
     const int ctas = c.ctas ? c.ctas : std::max(1, st->nsm - 4);
     const int threads = c.threads ? c.threads : 512;
-    const int tile_blocks = c.tile_blocks ? c.tile_blocks : 1024;
+    const int tile_blocks = c.tile_blocks ? c.tile_blocks : 256 * (threads / 32);  // one group per warp
     if (slots < 1 || slots > kMaxSlots || max_keys < 1 || max_keys > (1 << 20) || ctas < 1 ||
         ctas > st->nsm || threads < 32 || threads > 512 || (threads & 31) || tile_blocks < 256 ||
         tile_blocks % 256 || tile_blocks > (1 << 22))
@@ -565,8 +574,9 @@ int offload_submit(offload_server_t s, int key_slot, const uint8_t *iv, const vo
         return AES_ETOOBIG;
     const void *din = nullptr;
     void *dout = nullptr;
+    bool out_host = false;
     if (len) {
-        int rc = check_payload(in, out, len, s->device, &din, &dout);
+        int rc = check_payload(in, out, len, s->device, &din, &dout, &out_host);
         if (rc)
             return rc;
     }
@@ -605,6 +615,7 @@ int offload_submit(offload_server_t s, int key_slot, const uint8_t *iv, const vo
     iv_halves(iv, &hd.iv_hi, &hd.iv_lo);
     hd.gen = gen;
     hd.key_slot = (uint32_t)key_slot;
+    hd.flags = out_host ? 1u : 0u;
     const uint64_t tk = (gen << 16) | d;
     s->live[d].store(tk);
     const uint64_t seq = s->next_seq.fetch_add(1);
