@@ -221,8 +221,8 @@ typedef struct {
     uint64_t hbm_budget;    /* bytes of payload in flight at most (in + out,
                                in-place counted once); 0 = unlimited */
     int ctas;               /* resident CTAs; 0 = SM count - 4 */
-    int threads;            /* CTA size, multiple of 32, <= 512; 0 = 512 */
-    int tile_blocks;        /* 16-byte blocks per tile, multiple of 256; 0 = 256 per warp of a CTA */
+    int threads;            /* CTA size, multiple of 32, 64..768; 0 = 768 (warp 0 dispatches) */
+    int tile_blocks;        /* 16-byte blocks per tile: 64, 128 or a multiple of 256; 0 = per request (~512 tiles of 64..1024 blocks) */
     uint32_t idle_timeout_us; /* resident kernel exits after this long with no
                                  work (relaunched on the next submit); 0 = 200000 */
 } offload_cfg_t;
@@ -279,7 +279,9 @@ int offload_server_destroy(offload_server_t srv);
  * each submitted at its scheduled arrival_s (seconds from the call) or as
  * soon after as the thread can, and latency_us[i] = time from the scheduled
  * arrival to the moment the thread observes completion (-1 on error).
- * reqs must be sorted by arrival_s.  Host-side only; synchronous. */
+ * reqs must be sorted by arrival_s.  Host-side only; synchronous.  A thread
+ * that sees no completion for 30 s marks its remaining requests failed and
+ * the call returns AES_ETIMEOUT (a stuck or failed device). */
 typedef struct {
     int key_slot;       /* offload_drive: server key slot; aes_ctr_drive: index into ctxs */
     uint8_t iv[16];

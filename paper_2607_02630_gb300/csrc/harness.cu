@@ -33,7 +33,12 @@ struct Shared {
     std::atomic<uint64_t> bytes{0}, retries{0};
     std::atomic<int> errors{0};
     std::atomic<double> last_done{0.0};
+    std::atomic<bool> timed_out{false};
 };
+
+// A driver gives up when no request of its thread has completed for this
+// long (a stuck or failed device), marking what is left as failed.
+constexpr double kNoProgressSeconds = 30.0;
 
 void note_done(Shared &sh, double t)
 {
@@ -61,7 +66,17 @@ int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int 
         cudaSetDevice(dev);
         std::vector<std::pair<uint64_t, int>> pending;  // (ticket, request index)
         int next = k;
+        double last_progress = seconds_since(t0);
         while (next < n || !pending.empty()) {
+            if (seconds_since(t0) - last_progress > kNoProgressSeconds) {
+                sh.timed_out.store(true);
+                for (auto &pr : pending)
+                    latency_us[pr.second] = -1.0;
+                for (; next < n; next += nthreads)
+                    latency_us[next] = -1.0;
+                sh.errors.fetch_add((int)pending.size());
+                break;
+            }
             if (next < n && seconds_since(t0) >= reqs[next].arrival_s) {
                 const aes_drive_req_t &r = reqs[next];
                 uint64_t t = 0;
@@ -69,6 +84,7 @@ int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int 
                 if (rc == AES_OK) {
                     pending.emplace_back(t, next);
                     next += nthreads;
+                    last_progress = seconds_since(t0);
                 } else if (rc == AES_EAGAIN) {
                     sh.retries.fetch_add(1);  // back-pressure: poll below, then retry
                 } else {
@@ -85,6 +101,7 @@ int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int 
                 }
                 const int idx = pending[i].second;
                 const double now = seconds_since(t0);
+                last_progress = now;
                 if (rc == AES_OK) {
                     latency_us[idx] = (now - reqs[idx].arrival_s) * 1e6;
                     sh.bytes.fetch_add(reqs[idx].len);
@@ -108,7 +125,7 @@ int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int 
     res->bytes = sh.bytes.load();
     res->eagain_retries = sh.retries.load();
     res->errors = sh.errors.load();
-    return AES_OK;
+    return sh.timed_out.load() ? AES_ETIMEOUT : AES_OK;
 }
 
 int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, int n, int nthreads,
@@ -140,7 +157,17 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
         }
         std::vector<std::pair<cudaEvent_t, int>> pending;
         int next = k;
+        double last_progress = seconds_since(t0);
         while (next < n || !pending.empty()) {
+            if (seconds_since(t0) - last_progress > kNoProgressSeconds) {
+                sh.timed_out.store(true);
+                for (auto &pr : pending)
+                    latency_us[pr.second] = -1.0;
+                for (; next < n; next += nthreads)
+                    latency_us[next] = -1.0;
+                sh.errors.fetch_add((int)pending.size());
+                break;
+            }
             if (next < n && !free_ev.empty() && seconds_since(t0) >= reqs[next].arrival_s) {
                 const aes_drive_req_t &r = reqs[next];
                 const int rc = aes_ctr(ctxs[r.key_slot], r.iv, r.in, r.out, r.len, s);
@@ -148,6 +175,7 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
                 if (rc == AES_OK && cudaEventRecord(e, s) == cudaSuccess) {
                     free_ev.pop_back();
                     pending.emplace_back(e, next);
+                    last_progress = seconds_since(t0);
                 } else {
                     latency_us[next] = -1.0;
                     sh.errors.fetch_add(1);
@@ -162,6 +190,7 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
                 }
                 const int idx = pending[i].second;
                 const double now = seconds_since(t0);
+                last_progress = now;
                 if (q == cudaSuccess) {
                     latency_us[idx] = (now - reqs[idx].arrival_s) * 1e6;
                     sh.bytes.fetch_add(reqs[idx].len);
@@ -175,6 +204,9 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
                 pending.pop_back();
             }
         }
+        cudaStreamSynchronize(s);
+        for (auto &pr : pending)
+            free_ev.push_back(pr.first);
         for (cudaEvent_t e : free_ev)
             cudaEventDestroy(e);
         cudaStreamDestroy(s);
@@ -189,7 +221,7 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
     res->bytes = sh.bytes.load();
     res->eagain_retries = 0;
     res->errors = sh.errors.load();
-    return AES_OK;
+    return sh.timed_out.load() ? AES_ETIMEOUT : AES_OK;
 }
 
 }  // extern "C"

@@ -4,14 +4,14 @@
 // The paper reroutes an offload through a server's own concurrency: submit
 // the work to an executor, suspend the request, resume it on completion
 // (Sec. 3), detecting completion by polling (Sec. 6 setup).  Here "submit" is
-// offload_submit writing a descriptor and a queue entry, "suspend" is the
-// ticket it returns at once, and "resume" is offload_poll observing the
-// request's completion flag, which the GPU raises itself.
+// offload_submit writing a queue entry, "suspend" is the ticket it returns at
+// once, and "resume" is offload_poll observing the request's completion flag,
+// which the GPU raises itself.
 //
-// Host -> device (all in pinned mapped memory):
-//   descs[d]   request descriptor in slot d (pointers, length, IV, key slot, generation)
-//   queue[i]   entry of request sequence number s at i = s mod Q: {tag = s + 1, d}; the tag
-//              is stored last with release semantics
+// Host -> device (pinned mapped memory):
+//   queue[i]   entry of request sequence number s at i = s mod Q (64 bytes):
+//              payload pointers, length, IV, key slot, descriptor slot d,
+//              generation, flags, and the tag s + 1 stored last (release)
 //   stop       set by offload_server_destroy
 // Device -> host:
 //   done[d]    (generation << 2) | status, stored with st.release.sys once the last tile
@@ -19,16 +19,24 @@
 //   kstatus    exit reasons of the resident CTAs (bit mask)
 // Device-only state:
 //   cursor     seq (28 bits) | slot d (16 bits) | next tile (20 bits) of the request
-//              being cut into tiles; CTAs claim tiles with one atomicAdd
+//              being cut into tiles; tiles are claimed with atomicAdd
 //   adv        sequence number an elected CTA is advancing the cursor to
-//   recs[d]    validated copy of descs[d] with its tile count and a count of finished tiles
+//   recs[d]    validated copy of the request in slot d, its tile count and a count of
+//              finished tiles
 //
-// Requests are taken in submission order, but their tiles run on every
-// resident CTA at once, so requests that arrive while others are on the GPU
-// start as soon as a CTA frees up (continuous batching).  Every wait on the
-// device is bounded: a CTA with no work for idle_timeout exits (the host
-// relaunches the kernel on the next submit or poll), and the stop flag ends
-// all waits.
+// Each resident CTA is warp-specialised: warp 0 is the agent, the others are
+// workers.  The agent alone touches the global cursor: it claims tiles in
+// batches (as many as its workers are waiting for, plus a small prefetch) and
+// hands them to the workers through a ring in shared memory; when the current
+// request has no tiles left it either becomes the elected advancer (reads the
+// next queue entry, validates it into recs[d], moves the cursor) or waits for
+// the CTA that is.  A tile is tile_groups counter groups of one request and is
+// encrypted by one worker warp, so a request is spread over many SMs at once
+// and requests that arrive while others are on the GPU start as soon as an
+// agent asks for work (continuous batching).  Every wait on the device is
+// bounded: an agent with no new work for idle_timeout exits and its workers
+// follow once the ring is drained (the host relaunches the kernel on the
+// next submit or poll), and the stop flag ends every wait.
 #include "../../include/aesoffload.h"
 #include "internal.h"
 #include "runtime.h"
@@ -38,6 +46,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstddef>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -49,45 +58,52 @@ namespace {
 
 constexpr uint32_t kSeqMask = (1u << 28) - 1;
 constexpr uint32_t kTileBits = 20;
-constexpr uint32_t kMaxTiles = (1u << kTileBits) - 8192;  // headroom for exhausted claims
+constexpr uint32_t kTileMask = (1u << kTileBits) - 1;
+constexpr uint32_t kMaxTiles = (1u << kTileBits) - 16384;  // headroom for batched exhausted claims
 constexpr int kMaxSlots = 65535;
 constexpr uint32_t kExitStop = 1, kExitIdle = 2, kExitError = 4;
+constexpr int kMaxWarps = 24;   // CTA of at most 768 threads (80 registers each)
+constexpr uint32_t kRing = 64;  // >= workers + prefetch
+constexpr uint32_t kPrefetch = 1;
+constexpr uint32_t kMaxClaim = 2;    // tiles per claim: spreads a request over many SMs
+constexpr uint32_t kLookahead = 8;   // requests validated ahead of the cursor
+constexpr uint32_t kDispRing = 64;   // > kLookahead
 
-struct HostDesc {  // 64 bytes, host-written
+struct QEntry {  // 64 bytes, host-written, tag last
+    uint64_t tag;  // sequence number + 1
     uint64_t in, out, len, iv_hi, iv_lo, gen;
-    uint32_t key_slot, flags;  // flags bit 0: the output is pinned host memory
-    uint64_t pad1;
+    uint32_t key_slot;
+    uint16_t desc;   // slot index d
+    uint16_t flags;  // bit 0: the output is pinned host memory
 };
-static_assert(sizeof(HostDesc) == 64, "HostDesc layout");
-
-struct QEntry {
-    uint64_t tag;   // sequence number + 1, stored last
-    uint32_t desc;  // slot index
-    uint32_t pad;
-};
+static_assert(sizeof(QEntry) == 64, "QEntry layout");
 
 struct SrvRec {  // device-only, 128 bytes
-    aesrt::BatchReq rq;
+    aesrt::BatchReq rq;             // rq.pad holds the flags
     unsigned long long seq_ntiles;  // (seq << 20) | ntiles, written after the rest
     unsigned long long gen;
+    unsigned int tile_groups;       // this request's tile: tile_groups groups, or
+    unsigned int tile_parts;        // 1/tile_parts of one group
     unsigned int done_tiles;
-    unsigned int pad[11];
+    unsigned int pad[9];
 };
+static_assert(offsetof(SrvRec, tile_groups) % 8 == 0, "tile shape words are 8-byte aligned");
 static_assert(sizeof(SrvRec) == 128, "SrvRec layout");
 
 struct SrvParams {
     unsigned long long *cursor;
     unsigned long long *adv;
+    unsigned long long *disp;      // next sequence number to dispatch (validate into recs)
+    unsigned int *disp_slot;       // kDispRing: slot d of dispatched sequence number s at s % kDispRing
     SrvRec *recs;
     const uint4 *keys;          // max_keys x 15 round keys
     const int *key_nr;          // max_keys; 0 = unregistered
     const QEntry *queue;        // mapped
-    const HostDesc *descs;      // mapped
     unsigned long long *done;   // mapped
     const unsigned int *stop;   // mapped
     unsigned int *kstatus;      // mapped
     const uint32_t *te0;
-    uint32_t qmask, max_keys, tile_groups, nslots;
+    uint32_t qmask, max_keys, tile_blocks, nslots;  // tile_blocks 0 = chosen per request
     uint64_t idle_ns, max_len;
 };
 
@@ -102,6 +118,10 @@ __device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t *p)
     uint64_t v;
     asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+__device__ __forceinline__ void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
+{
+    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 __device__ __forceinline__ uint64_t ld_relaxed_gpu(const unsigned long long *p)
 {
@@ -121,25 +141,130 @@ __device__ __forceinline__ uint32_t ld_volatile(const unsigned int *p)
 {
     return *reinterpret_cast<const volatile unsigned int *>(p);
 }
-__device__ __forceinline__ uint64_t ld_volatile64(const uint64_t *p)
+
+// The stop flag lives in host memory (one NVLink-C2C round trip per read),
+// so spinning loops look at it at most every 50 us.
+struct StopCheck {
+    uint64_t next = 0;
+    __device__ __forceinline__ bool operator()(const unsigned int *flag)
+    {
+        const uint64_t now = gtime();
+        if (now < next)
+            return false;
+        next = now + 50000;
+        return ld_volatile(flag) != 0;
+    }
+};
+
+// Dispatch request k if its queue entry is present and nobody else has:
+// validate it into recs[d] (the tile count and sequence number last) and
+// note its slot in disp_slot.  Requests are dispatched in sequence order, one
+// dispatcher per request (the CAS on disp), and only ahead of the cursor.
+// Returns true if this thread dispatched k.
+__device__ bool try_dispatch(const SrvParams &p, uint32_t k, uint32_t *slot = nullptr)
 {
-    return *reinterpret_cast<const volatile uint64_t *>(p);
+    const QEntry *q = p.queue + (k & p.qmask);
+    const uint64_t tag = ld_acquire_sys(&q->tag);
+    if ((uint32_t)(tag & kSeqMask) != ((k + 1) & kSeqMask))
+        return false;  // not submitted yet
+    if (atomicCAS(p.disp, (unsigned long long)k, (unsigned long long)((k + 1) & kSeqMask)) != k)
+        return false;  // someone else dispatches it
+    // the rest of the entry, after the acquire of its tag: four independent 16-byte loads
+    const uint64_t *e = reinterpret_cast<const uint64_t *>(q);
+    uint64_t x1, x2, x3, x4, x5, x6, x7, unused;
+    ld_volatile_v2(e + 0, unused, x1);
+    ld_volatile_v2(e + 2, x2, x3);
+    ld_volatile_v2(e + 4, x4, x5);
+    ld_volatile_v2(e + 6, x6, x7);
+    (void)unused;
+    const uint64_t in = x1, out = x2, len = x3, iv_hi = x4, iv_lo = x5, gen = x6;
+    const uint32_t ks = (uint32_t)x7;
+    const uint32_t d = (uint32_t)(x7 >> 32) & 0xffffu;
+    const uint32_t flags = (uint32_t)(x7 >> 48);
+    if (d >= p.nslots) {  // the host never writes such an entry; the advancer stops on it
+        *reinterpret_cast<volatile unsigned int *>(p.disp_slot + (k % kDispRing)) = 0xffffffffu;
+        if (slot)
+            *slot = 0xffffffffu;
+        return true;
+    }
+    int nr = 0;
+    if (ks < p.max_keys)
+        nr = __ldcg(p.key_nr + ks);
+    bool ok = (nr == 10 || nr == 12 || nr == 14) && len <= p.max_len;
+    if (ok && len)
+        ok = in && out && !((in | out) & 15u);
+    uint32_t ntiles = 0, tg = 1, tp = 1;
+    if (ok && len) {
+        // tiles are runs of tg whole 256-block counter groups, or (tp > 1)
+        // equal parts of one group.  Unless fixed by the server config, a
+        // request is cut into about 512 tiles of 64..1024 blocks: short
+        // requests spread over many warps, long ones keep claims rare.
+        const uint64_t nb = (len + 15) >> 4;
+        const uint64_t groups = (((iv_lo & 255u) + nb - 1) >> 8) + 1;
+        uint32_t tb = p.tile_blocks;
+        if (!tb) {
+            tb = 64;
+            while (tb < 1024 && (uint64_t)tb * 512 < nb)
+                tb <<= 1;
+        }
+        if (tb >= 256)
+            tg = tb / 256;
+        else
+            tp = 256 / tb;
+        ntiles = (uint32_t)((groups + tg - 1) / tg * tp);
+    }
+    SrvRec *rec = p.recs + d;
+    rec->rq.in = reinterpret_cast<const uint4 *>(in);
+    rec->rq.out = reinterpret_cast<uint4 *>(out);
+    rec->rq.len = len;
+    rec->rq.iv_hi = iv_hi;
+    rec->rq.iv_lo = iv_lo;
+    rec->rq.rk = p.keys + 15u * (ok ? ks : 0u);
+    rec->rq.nr = (uint32_t)nr;
+    rec->rq.pad = flags;
+    rec->gen = gen;
+    rec->done_tiles = 0;
+    rec->tile_groups = tg;
+    rec->tile_parts = tp;
+    *reinterpret_cast<volatile unsigned int *>(p.disp_slot + (k % kDispRing)) = d;
+    __threadfence();
+    st_relaxed_gpu(&rec->seq_ntiles, ((uint64_t)k << kTileBits) | ntiles);
+    if (slot)
+        *slot = d;
+    if (ntiles == 0) {
+        __threadfence_system();
+        st_release_sys(p.done + d, (gen << 2) | (ok ? 1u : 2u));
+    }
+    return true;
 }
 
-// Elected advancer: wait for request nseq = seq + 1 in the queue, validate
-// and copy it into recs[d], then move the cursor to it.  Returns 0 or an
-// exit code (after handing the advancer role back).
-__device__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_work)
+// Elected advancer: move the cursor from request seq to request seq + 1 once
+// that request is dispatched (dispatching it here if nobody has), then
+// dispatch what is already queued behind it, up to kLookahead ahead.
+// Returns 0 or an exit code (after handing the advancer role back).
+__device__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_work, StopCheck &stop)
 {
     const uint32_t nseq = (seq + 1) & kSeqMask;
-    const uint32_t idx = nseq & p.qmask;
-    const uint32_t want = (nseq + 1) & kSeqMask;
+    uint32_t d = 0;
     for (;;) {
-        const uint64_t tag = ld_acquire_sys(&p.queue[idx].tag);
-        if ((uint32_t)(tag & kSeqMask) == want)
-            break;
+        const uint32_t dsp = (uint32_t)ld_relaxed_gpu(p.disp);
+        if (dsp == nseq) {
+            // not dispatched yet: do it if it is queued (then its slot is known)
+            if (try_dispatch(p, nseq, &d)) {
+                if (d >= p.nslots)
+                    return kExitError;
+                break;
+            }
+        } else {
+            d = *reinterpret_cast<const volatile unsigned int *>(p.disp_slot + (nseq % kDispRing));
+            if (d >= p.nslots)
+                return kExitError;
+            const uint64_t sn = ld_relaxed_gpu(&p.recs[d].seq_ntiles);
+            if ((uint32_t)(sn >> kTileBits) == nseq)
+                break;  // dispatched and fully written
+        }
         uint32_t r = 0;
-        if (ld_volatile(p.stop))
+        if (stop(p.stop))
             r = kExitStop;
         else if (gtime() - last_work > p.idle_ns)
             r = kExitIdle;
@@ -147,42 +272,8 @@ __device__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_wor
             atomicCAS(p.adv, (unsigned long long)nseq, (unsigned long long)seq);
             return r;
         }
-        __nanosleep(128);
+        __nanosleep(32);
     }
-    const uint32_t d = ld_volatile(&p.queue[idx].desc);
-    if (d >= p.nslots)
-        return kExitError;  // the host never writes such an entry
-    const HostDesc *hd = p.descs + d;
-    const uint64_t in = ld_volatile64(&hd->in), out = ld_volatile64(&hd->out);
-    const uint64_t len = ld_volatile64(&hd->len), gen = ld_volatile64(&hd->gen);
-    const uint32_t ks = ld_volatile(&hd->key_slot);
-    int nr = 0;
-    if (ks < p.max_keys)
-        nr = __ldcg(p.key_nr + ks);
-    bool ok = (nr == 10 || nr == 12 || nr == 14) && len <= p.max_len;
-    if (ok && len)
-        ok = in && out && !((in | out) & 15u);
-    uint32_t ntiles = 0;
-    const uint64_t iv_lo = ld_volatile64(&hd->iv_lo);
-    if (ok && len) {
-        // tiles are runs of tile_groups whole 256-block counter groups
-        const uint64_t nb = (len + 15) >> 4;
-        const uint64_t groups = (((iv_lo & 255u) + nb - 1) >> 8) + 1;
-        ntiles = (uint32_t)((groups + p.tile_groups - 1) / p.tile_groups);
-    }
-    SrvRec *rec = p.recs + d;
-    rec->rq.in = reinterpret_cast<const uint4 *>(in);
-    rec->rq.out = reinterpret_cast<uint4 *>(out);
-    rec->rq.len = len;
-    rec->rq.iv_hi = ld_volatile64(&hd->iv_hi);
-    rec->rq.iv_lo = iv_lo;
-    rec->rq.rk = p.keys + 15u * (ok ? ks : 0u);
-    rec->rq.nr = (uint32_t)nr;
-    rec->rq.pad = ld_volatile(&hd->flags);
-    rec->gen = gen;
-    rec->done_tiles = 0;
-    __threadfence();
-    st_relaxed_gpu(&rec->seq_ntiles, ((uint64_t)nseq << kTileBits) | ntiles);
     __threadfence();
     unsigned long long cur = ld_relaxed_gpu(p.cursor);
     const unsigned long long nv = ((unsigned long long)nseq << 36) | ((unsigned long long)d << kTileBits);
@@ -194,118 +285,204 @@ __device__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_wor
             break;
         cur = old;
     }
-    if (ntiles == 0) {
-        __threadfence_system();
-        st_release_sys(p.done + d, (gen << 2) | (ok ? 1u : 2u));
-    }
     last_work = gtime();
+    // look ahead: validate requests already queued behind the new one
+    for (;;) {
+        const uint32_t k = (uint32_t)ld_relaxed_gpu(p.disp);
+        if (((k - nseq) & kSeqMask) > kLookahead || !try_dispatch(p, k))
+            break;
+    }
     return 0;
 }
 
-// Claim the next tile (thread 0 of a CTA).  Returns 0 with *d, *t set, or an
-// exit code.
-__device__ uint32_t acquire(const SrvParams &p, uint64_t &last_work, uint32_t *d_out, uint32_t *t_out)
+// Claim up to `want` tiles of the current request (the agent of a CTA).
+// Returns 0 with the tiles [*t0, *t1) of slot *d and its sequence number, or
+// an exit code.
+__device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &stop, uint32_t want,
+                          uint32_t *d_out, uint32_t *seq_out, uint32_t *t0, uint32_t *t1)
 {
     for (;;) {
-        if (ld_volatile(p.stop))
+        if (stop(p.stop))
             return kExitStop;
-        const unsigned long long v = atomicAdd(p.cursor, 1ull);
+        const unsigned long long v = atomicAdd(p.cursor, (unsigned long long)want);
         const uint32_t seq = (uint32_t)(v >> 36);
         const uint32_t d = (uint32_t)(v >> kTileBits) & 0xffffu;
-        const uint32_t t = (uint32_t)v & ((1u << kTileBits) - 1);
+        const uint32_t t = (uint32_t)v & kTileMask;
         if (d < p.nslots) {
             const uint64_t sn = ld_relaxed_gpu(&p.recs[d].seq_ntiles);
-            if ((uint32_t)(sn >> kTileBits) == seq && t < (uint32_t)(sn & ((1u << kTileBits) - 1))) {
+            const uint32_t nt = (uint32_t)(sn & kTileMask);
+            if ((uint32_t)(sn >> kTileBits) == seq && t < nt) {
                 *d_out = d;
-                *t_out = t;
+                *seq_out = seq;
+                *t0 = t;
+                *t1 = t + want < nt ? t + want : nt;
+                last_work = gtime();
                 return 0;
             }
         }
         // The current request has no tiles left: advance, or wait for the
         // CTA that does.
         if (atomicCAS(p.adv, (unsigned long long)seq, (unsigned long long)((seq + 1) & kSeqMask)) == seq) {
-            const uint32_t r = advance(p, seq, last_work);
+            const uint32_t r = advance(p, seq, last_work, stop);
             if (r)
                 return r;
         } else {
-            for (;;) {
+            for (uint32_t spin = 0;; ++spin) {
                 if ((uint32_t)(ld_relaxed_gpu(p.cursor) >> 36) != seq)
                     break;
-                if ((uint32_t)ld_relaxed_gpu(p.adv) == seq)
+                if ((spin & 7) == 7 && (uint32_t)ld_relaxed_gpu(p.adv) == seq)
                     break;  // the advancer gave up its role: compete for it again
-                if (ld_volatile(p.stop))
+                if (stop(p.stop))
                     return kExitStop;
                 if (gtime() - last_work > p.idle_ns)
                     return kExitIdle;
-                __nanosleep(128);
+                __nanosleep(100);
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ SrvParams p)
+struct Ring {
+    unsigned int head;               // positions reserved by workers (atomicAdd)
+    volatile unsigned int tail;      // positions filled by the agent
+    volatile unsigned int exit_code; // set by the agent after its last push
+    uint32_t d[kRing], t[kRing], seq[kRing];
+    volatile unsigned int read_mark[kRing];  // position + 1 of the last item read from each slot
+};
+
+// Agent warp, lane 0: keep the ring kPrefetch items ahead of the workers.
+__device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
+{
+    uint64_t last_work = gtime();
+    StopCheck stop;
+    uint32_t ld = 0, lseq = 0, lt = 0, lend = 0;  // current lease: tiles [lt, lend) of slot ld
+    uint32_t code = 0;
+    for (;;) {
+        const uint32_t head = *reinterpret_cast<volatile unsigned int *>(&ring.head);
+        const uint32_t tail = ring.tail;
+        // full: kPrefetch items already wait for workers, or the item that
+        // position tail would overwrite (tail - kRing) has not been read yet
+        if ((int32_t)(tail - head) >= (int32_t)kPrefetch ||
+            (tail >= kRing && ring.read_mark[tail % kRing] != tail - kRing + 1)) {
+            if (stop(p.stop)) {
+                code = kExitStop;
+                break;
+            }
+            continue;  // the workers drain the ring within microseconds: spin
+        }
+        if (lt >= lend) {
+            const uint32_t waiting = (int32_t)(head - tail) > 0 ? head - tail : 0u;
+            const uint32_t want = waiting + kPrefetch < kMaxClaim ? waiting + kPrefetch : kMaxClaim;
+            code = claim(p, last_work, stop, want, &ld, &lseq, &lt, &lend);
+            if (code)
+                break;
+        }
+        const uint32_t slot = tail % kRing;
+        ring.d[slot] = ld;
+        ring.t[slot] = lt;
+        ring.seq[slot] = lseq;
+        ++lt;
+        __threadfence_block();
+        ring.tail = tail + 1;
+    }
+    __threadfence_block();
+    ring.exit_code = code;
+}
+
+__global__ void __launch_bounds__(768, 1) server_kernel(const __grid_constant__ SrvParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint4 s_rk[15];
-    __shared__ int s_cmd;
-    __shared__ uint32_t s_tile;
+    __shared__ Ring ring;
+    __shared__ uint4 s_rk[kMaxWarps][15];  // round keys of each worker's current request
+    if (threadIdx.x == 0) {
+        ring.head = 0;
+        ring.tail = 0;
+        ring.exit_code = 0;
+        for (uint32_t i = 0; i < kRing; ++i)
+            ring.read_mark[i] = 0;
+    }
     aestt::fill_tables(smem, p.te0);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        if (lane == 0) {
+            agent(p, ring);
+            if (ring.exit_code)
+                atomicOr_system(p.kstatus, ring.exit_code);
+        }
+        return;  // no CTA-wide barrier follows
+    }
     const aestt::Lanes ln;
-    uint64_t last_work = gtime();  // used by thread 0
-    // Thread 0 claims a tile for the whole CTA (so at most one poller per
-    // CTA touches the cursor); a tile is tile_groups counter groups, one per
-    // warp by default, so the per-tile barrier waits for no straggler.
+    uint4 *w_rk = s_rk[warp];
+    uint32_t cur_d = ~0u, cur_seq = ~0u, tg = 1, tp = 1;
+    aesrt::BatchReq rq;
     for (;;) {
-        if (threadIdx.x == 0) {
-            uint32_t d = 0, t = 0;
-            const uint32_t r = acquire(p, last_work, &d, &t);
-            s_cmd = r ? -(int)r : (int)d;
-            s_tile = t;
+        uint32_t d = 0, t = 0, seq = 0, quit = 0;
+        if (lane == 0) {
+            const uint32_t pos = atomicAdd(&ring.head, 1u);
+            for (;;) {
+                if ((int32_t)(ring.tail - pos) > 0)
+                    break;
+                if (ring.exit_code) {
+                    __threadfence_block();
+                    quit = (int32_t)(ring.tail - pos) <= 0;  // the agent's last pushes come first
+                    break;
+                }
+            }
+            if (!quit) {
+                __threadfence_block();
+                d = ring.d[pos % kRing];
+                t = ring.t[pos % kRing];
+                seq = ring.seq[pos % kRing];
+                __threadfence_block();
+                ring.read_mark[pos % kRing] = pos + 1;
+            }
         }
-        __syncthreads();  // also publishes the tables on the first pass
-        const int cmd = s_cmd;
-        if (cmd < 0) {
-            if (threadIdx.x == 0)
-                atomicOr_system(p.kstatus, (unsigned int)(-cmd));
+        quit = __shfl_sync(0xffffffffu, quit, 0);
+        if (quit)
             break;
-        }
-        SrvRec *rec = p.recs + cmd;
-        aesrt::BatchReq rq;
-        {
+        d = __shfl_sync(0xffffffffu, d, 0);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        seq = __shfl_sync(0xffffffffu, seq, 0);
+        SrvRec *rec = p.recs + d;
+        if (d != cur_d || seq != cur_seq) {  // a new request for this warp: load it and its keys
             const uint4 *src = reinterpret_cast<const uint4 *>(&rec->rq);
             uint4 *dst = reinterpret_cast<uint4 *>(&rq);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 dst[i] = __ldcg(src + i);
+            tg = __ldcg(&rec->tile_groups);
+            tp = __ldcg(&rec->tile_parts);
+            __syncwarp();
+            if (lane <= rq.nr)
+                w_rk[lane] = __ldcg(rq.rk + lane);
+            __syncwarp();
+            cur_d = d;
+            cur_seq = seq;
         }
-        if (threadIdx.x <= rq.nr)
-            s_rk[threadIdx.x] = __ldcg(rq.rk + threadIdx.x);
-        const uint32_t tile = s_tile;
-        __syncthreads();
         uint64_t first, last;
-        aestile::tile_blocks_of(tile, p.tile_groups, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
+        const uint32_t part = t % tp;
+        aestile::tile_blocks_of(t / tp, tg, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
         switch (rq.nr) {
-        case 10: aestile::run_tile<10, 2>(rq, first, last, smem, ln, s_rk); break;
-        case 12: aestile::run_tile<12, 2>(rq, first, last, smem, ln, s_rk); break;
-        default: aestile::run_tile<14, 2>(rq, first, last, smem, ln, s_rk); break;
+        case 10: aestile::run_tile_warp<10, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
+        case 12: aestile::run_tile_warp<12, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
+        default: aestile::run_tile_warp<14, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
         }
-        // Order this thread's output stores before the tile is counted: at
+        // Order this lane's output stores before the tile is counted: at
         // system scope when the output lives in host memory, else GPU scope
         // (the completing thread's system-scope release covers the rest).
         if (rq.pad & 1u)
             __threadfence_system();
         else
             __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const uint32_t ntiles = (uint32_t)(ld_relaxed_gpu(&rec->seq_ntiles) & ((1u << kTileBits) - 1));
-            const uint64_t gen = __ldcg(&rec->gen);
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t ntiles = (uint32_t)(ld_relaxed_gpu(&rec->seq_ntiles) & kTileMask);
             const unsigned int prev = atomicAdd(&rec->done_tiles, 1u);
             if (prev + 1 == ntiles) {
                 __threadfence_system();
-                st_release_sys(p.done + cmd, (gen << 2) | 1u);
+                st_release_sys(p.done + d, (__ldcg(&rec->gen) << 2) | 1u);
             }
-            last_work = gtime();
         }
     }
 }
@@ -320,7 +497,6 @@ struct offload_server_s {
     uint32_t qsize = 0;
     uint64_t budget = 0, max_len = 0, idle_ns = 0;
     // mapped host memory
-    HostDesc *descs = nullptr;
     QEntry *queue = nullptr;
     unsigned long long *done = nullptr;
     unsigned int *ctrl = nullptr;  // [0] stop, [1] kernel exit status
@@ -334,14 +510,15 @@ struct offload_server_s {
     std::vector<uint32_t> free_slots;
     std::vector<uint64_t> gen;     // per slot, current generation
     std::vector<uint64_t> bytes;   // per slot, budget charged
+    std::vector<uint64_t> lens;    // per slot, payload length
     std::unique_ptr<std::atomic<uint64_t>[]> live;  // per slot, live ticket (0 = free)
     std::vector<int> key_used;
     std::atomic<uint64_t> next_seq{1};
     std::atomic<uint64_t> inflight{0};
     std::atomic<bool> stopping{false};
-    std::atomic<int> running{0};
     std::atomic<uint64_t> n_sub{0}, n_done{0}, n_again{0}, n_err{0}, n_relaunch{0}, n_bytes{0};
     uint32_t last_status = 0;
+    std::atomic<int64_t> next_query_ns{0};  // when the kernel's stream is queried next
 };
 
 namespace {
@@ -353,7 +530,6 @@ int launch_resident(offload_server_s *s)
     cudaError_t e = cudaGetLastError();
     if (e)
         return cuda_fail(e, "server_kernel launch");
-    s->running.store(1);
     return AES_OK;
 }
 
@@ -362,6 +538,16 @@ int ensure_running(offload_server_s *s)
 {
     if (s->stopping.load())
         return AES_ESTOPPED;
+    // CTAs raise their exit reason in the mapped status word before they
+    // end, so while it is clear the kernel is running -- unless it died on
+    // a fault, which only a stream query shows: query at most every 1 ms.
+    const int64_t now = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                            std::chrono::steady_clock::now().time_since_epoch()).count();
+    if (__atomic_load_n(&s->ctrl[1], __ATOMIC_ACQUIRE) == 0) {
+        int64_t next = s->next_query_ns.load();
+        if (now < next || !s->next_query_ns.compare_exchange_strong(next, now + 1000000))
+            return AES_OK;
+    }
     cudaError_t q = cudaStreamQuery(s->stream);
     if (q == cudaErrorNotReady)
         return AES_OK;
@@ -372,7 +558,6 @@ int ensure_running(offload_server_s *s)
     if (q != cudaSuccess)
         return cuda_fail(q, "resident kernel");
     s->last_status = s->ctrl[1];
-    s->running.store(0);
     if (s->last_status & kExitError)
         return AES_ECUDA;
     s->n_relaunch.fetch_add(1);
@@ -405,11 +590,14 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     const int slots = c.slots ? c.slots : 1024;
     const int max_keys = c.max_keys ? c.max_keys : 64;
     const int ctas = c.ctas ? c.ctas : std::max(1, st->nsm - 4);
-    const int threads = c.threads ? c.threads : 512;
-    const int tile_blocks = c.tile_blocks ? c.tile_blocks : 256 * (threads / 32);  // one group per warp
+    const int threads = c.threads ? c.threads : 768;
+    const int tile_blocks = c.tile_blocks;  // 0: chosen per request
+    // warp 0 of each CTA is the agent, so at least one worker warp is needed
     if (slots < 1 || slots > kMaxSlots || max_keys < 1 || max_keys > (1 << 20) || ctas < 1 ||
-        ctas > st->nsm || threads < 32 || threads > 512 || (threads & 31) || tile_blocks < 256 ||
-        tile_blocks % 256 || tile_blocks > (1 << 22))
+        ctas > st->nsm || threads < 64 || threads > 32 * kMaxWarps || (threads & 31) ||
+        !(tile_blocks == 0 || tile_blocks == 64 || tile_blocks == 128 ||
+          (tile_blocks >= 256 && tile_blocks % 256 == 0)) ||
+        tile_blocks > (1 << 22))
         return AES_EINVAL;
     offload_server_s *s = new (std::nothrow) offload_server_s();
     if (!s)
@@ -422,7 +610,9 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     s->tile_blocks = tile_blocks;
     s->budget = c.hbm_budget;
     s->idle_ns = 1000ull * (c.idle_timeout_us ? c.idle_timeout_us : 200000u);
-    s->max_len = std::min<uint64_t>(16ull << 30, ((uint64_t)kMaxTiles - 1) * (uint64_t)tile_blocks * 16u);
+    // tiles of at least 64 blocks (1024 adaptive for long requests) keep the tile count < kMaxTiles
+    s->max_len = std::min<uint64_t>(16ull << 30, ((uint64_t)kMaxTiles - 1) *
+                                                   (uint64_t)(tile_blocks ? tile_blocks : 1024) * 16u);
     uint32_t q = 1;
     while (q < (uint32_t)slots)
         q <<= 1;
@@ -432,6 +622,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
         s->free_slots.push_back((uint32_t)i);
     s->gen.assign(slots, 0);
     s->bytes.assign(slots, 0);
+    s->lens.assign(slots, 0);
     s->live.reset(new std::atomic<uint64_t>[slots]);
     for (int i = 0; i < slots; ++i)
         s->live[i].store(0);
@@ -444,7 +635,6 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
         if (s->setup)
             cudaStreamDestroy(s->setup);
         cudaFree(s->dmem);
-        cudaFreeHost(s->descs);
         cudaFreeHost(s->queue);
         cudaFreeHost(s->done);
         cudaFreeHost(s->ctrl);
@@ -452,20 +642,20 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
         return e == cudaErrorMemoryAllocation ? AES_ENOMEM : cuda_fail(e, where);
     };
     const unsigned flags = cudaHostAllocMapped | cudaHostAllocPortable;
-    if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->descs), sizeof(HostDesc) * slots, flags)))
-        return fail("cudaHostAlloc(descs)");
     if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->queue), sizeof(QEntry) * q, flags)))
         return fail("cudaHostAlloc(queue)");
     if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->done), sizeof(unsigned long long) * slots, flags)))
         return fail("cudaHostAlloc(done)");
     if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->ctrl), 64, flags)))
         return fail("cudaHostAlloc(ctrl)");
-    std::memset(s->descs, 0, sizeof(HostDesc) * slots);
     std::memset(s->queue, 0, sizeof(QEntry) * q);
     std::memset(s->done, 0, sizeof(unsigned long long) * slots);
     std::memset(s->ctrl, 0, 64);
-    // device: [cursor, adv][recs][keys][key_nr]
-    const size_t off_recs = 256;
+    // device: cursor, adv and disp each on a 4 KiB page of their own (every
+    // agent polls them), then disp_slot, recs, keys, key_nr
+    const size_t off_adv = 4096, off_disp = 8192, off_slots = 12288;
+    const size_t off_recs = 16384;
+    static_assert(4 * kDispRing <= 4096, "disp_slot fits in its page");
     const size_t off_keys = off_recs + sizeof(SrvRec) * (size_t)slots;
     const size_t off_nr = off_keys + 240 * (size_t)max_keys;
     const size_t dbytes = off_nr + sizeof(int) * (size_t)max_keys;
@@ -475,11 +665,16 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
         return fail("cudaStreamCreate");
     if ((e = cudaStreamCreateWithFlags(&s->setup, cudaStreamNonBlocking)))
         return fail("cudaStreamCreate");
-    if ((e = cudaMemsetAsync(s->dmem, 0, dbytes, s->setup)) || (e = cudaStreamSynchronize(s->setup)))
+    const unsigned long long first_seq = 1;  // request sequence numbers start at 1
+    if ((e = cudaMemsetAsync(s->dmem, 0, dbytes, s->setup)) ||
+        (e = cudaMemcpyAsync(s->dmem + off_disp, &first_seq, 8, cudaMemcpyHostToDevice, s->setup)) ||
+        (e = cudaStreamSynchronize(s->setup)))
         return fail("cudaMemset(server)");
     SrvParams &P = s->params;
     P.cursor = reinterpret_cast<unsigned long long *>(s->dmem);
-    P.adv = reinterpret_cast<unsigned long long *>(s->dmem + 8);
+    P.adv = reinterpret_cast<unsigned long long *>(s->dmem + off_adv);
+    P.disp = reinterpret_cast<unsigned long long *>(s->dmem + off_disp);
+    P.disp_slot = reinterpret_cast<unsigned int *>(s->dmem + off_slots);
     P.recs = reinterpret_cast<SrvRec *>(s->dmem + off_recs);
     P.keys = reinterpret_cast<const uint4 *>(s->dmem + off_keys);
     P.key_nr = reinterpret_cast<const int *>(s->dmem + off_nr);
@@ -487,9 +682,6 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     if ((e = cudaHostGetDevicePointer(&dp, s->queue, 0)))
         return fail("cudaHostGetDevicePointer");
     P.queue = static_cast<const QEntry *>(dp);
-    if ((e = cudaHostGetDevicePointer(&dp, s->descs, 0)))
-        return fail("cudaHostGetDevicePointer");
-    P.descs = static_cast<const HostDesc *>(dp);
     if ((e = cudaHostGetDevicePointer(&dp, s->done, 0)))
         return fail("cudaHostGetDevicePointer");
     P.done = static_cast<unsigned long long *>(dp);
@@ -500,7 +692,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     P.te0 = st->te0;
     P.qmask = q - 1;
     P.max_keys = (uint32_t)max_keys;
-    P.tile_groups = (uint32_t)(tile_blocks / 256);
+    P.tile_blocks = (uint32_t)tile_blocks;
     P.nslots = (uint32_t)slots;
     P.idle_ns = s->idle_ns;
     P.max_len = s->max_len;
@@ -608,19 +800,22 @@ int offload_submit(offload_server_t s, int key_slot, const uint8_t *iv, const vo
     }
     const uint64_t gen = ++s->gen[d];
     s->bytes[d] = charge;
-    HostDesc &hd = s->descs[d];
-    hd.in = (uint64_t)(uintptr_t)din;
-    hd.out = (uint64_t)(uintptr_t)dout;
-    hd.len = len;
-    iv_halves(iv, &hd.iv_hi, &hd.iv_lo);
-    hd.gen = gen;
-    hd.key_slot = (uint32_t)key_slot;
-    hd.flags = out_host ? 1u : 0u;
+    s->lens[d] = len;
     const uint64_t tk = (gen << 16) | d;
     s->live[d].store(tk);
+    // A slot is admitted only while fewer than `slots` requests are in
+    // flight and the device reads entries in sequence order, so the entry of
+    // seq - qsize (qsize >= slots) has been read before this one reuses it.
     const uint64_t seq = s->next_seq.fetch_add(1);
     QEntry &qe = s->queue[seq & (s->qsize - 1)];
-    qe.desc = d;
+    qe.in = (uint64_t)(uintptr_t)din;
+    qe.out = (uint64_t)(uintptr_t)dout;
+    qe.len = len;
+    iv_halves(iv, &qe.iv_hi, &qe.iv_lo);
+    qe.gen = gen;
+    qe.key_slot = (uint32_t)key_slot;
+    qe.desc = (uint16_t)d;
+    qe.flags = out_host ? 1u : 0u;
     __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
     s->n_sub.fetch_add(1);
     *ticket = tk;
@@ -647,7 +842,7 @@ int offload_poll(offload_server_t s, uint64_t ticket)
     if (!s->live[d].compare_exchange_strong(expect, 0))
         return AES_EINVAL;  // another thread released it first
     const uint32_t status = (uint32_t)(v & 3u);
-    const uint64_t nbytes = s->descs[d].len;
+    const uint64_t nbytes = s->lens[d];
     release_slot(s, d);
     if (status != 1) {
         s->n_err.fetch_add(1);
@@ -707,7 +902,6 @@ int offload_server_destroy(offload_server_t s)
     cudaStreamDestroy(s->stream);
     cudaStreamDestroy(s->setup);
     cudaFree(s->dmem);
-    cudaFreeHost(s->descs);
     cudaFreeHost(s->queue);
     cudaFreeHost(s->done);
     cudaFreeHost(s->ctrl);
