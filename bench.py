@@ -34,6 +34,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2607_02630_gb300 import replicas as R  # noqa: E402
 from paper_2607_02630_gb300 import workloads as W  # noqa: E402
 
 METRIC = "AES-CTR GB/s (% roofline) batched vs per-call; p50/p99 1 MiB offload µs"
@@ -113,10 +114,7 @@ class ClockSampler:
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return R.world_from_env()
 
 
 KERNEL_SOURCES = ["paper_2607_02630_gb300/csrc/batch.cu", "paper_2607_02630_gb300/csrc/tile.cuh",
@@ -198,24 +196,31 @@ def run_oracle(w, idx, nthreads: int) -> float:
     return time.perf_counter() - t0
 
 
+def workload_name(requests: int) -> str:
+    return WORKLOAD if requests == 4096 else f"{requests} requests of: " + WORKLOAD
+
+
 def reference_arm(args, ws, rank):
     if rank != 0:
         return 0
     nthreads = os.cpu_count() or 1
-    w = W.batch_varlen(seed=W.SEED_BASE + 3)
-    per_step_s = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    w = W.batch_varlen(n=args.requests, seed=W.SEED_BASE + 3)
+    per_step_s = args.reference_step_seconds
+    if per_step_s is None:
+        per_step_s = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
     idx, nbytes = oracle_sample(w, per_step_s, nthreads)
     for _ in range(args.warmup):
         run_oracle(w, idx[:1], nthreads)
     times = [run_oracle(w, idx, nthreads) for _ in range(args.steps)]
     total = sum(times)
     value = nbytes * args.steps / total / 1e9
-    sample = f"first {len(idx)} of 4096 requests ({nbytes / 1e6:.1f} MB) per step, oracle_ctr_mt"
+    sample = f"first {len(idx)} of {w.n} requests ({nbytes / 1e6:.1f} MB) per step, oracle_ctr_mt"
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "global_batch": 4096, "seq_len": None,
+        "data": "synthetic", "config": {"workload": workload_name(args.requests),
+                                        "global_batch": args.requests * args.gpus, "seq_len": None,
                                         "parallelism": f"replicas{args.gpus}"},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": nthreads, "kind": "oracle",
                          "sample": sample},
@@ -473,6 +478,8 @@ def main():
     ap.add_argument("--requests", type=int, default=4096,
                     help="requests per step (4096 = the benchmark workload; fewer only for profiler captures)")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--reference-step-seconds", type=float, default=None,
+                    help="CPU seconds of oracle work per --impl reference step (default: fit the run in ~150 s)")
     ap.add_argument("--sweep", action="store_true",
                     help="single-buffer sweep instead of the batch step: sizes x key sizes x variants")
     ap.add_argument("--sweep-sizes", default="4096,16384,65536,262144,1048576,4194304,16777216,67108864,268435456")
@@ -509,7 +516,7 @@ def main():
     sh = int(stream.cuda_stream)
 
     # ---- workload, resident in HBM
-    w = W.batch_varlen(n=args.requests, seed=W.SEED_BASE + 3 + 1000 * rank)
+    w = W.batch_varlen(n=args.requests, seed=R.rank_seed(W.SEED_BASE + 3, rank))
     src = torch.from_numpy(w.payload).to(dev)
     dst = torch.empty(w.arena_bytes, dtype=torch.uint8, device=dev)
     ctxs = [A.Context(w.key_of(i).tobytes(), int(w.bits[i])) for i in range(w.n)]
@@ -542,11 +549,8 @@ def main():
     barrier()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     per_launch = [a.elapsed_time(b) / 1e3 for a, b in ev]
-    if dist:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = ws * step_bytes * args.steps / elapsed / 1e9
+    elapsed = R.max_over_ranks(elapsed, dist, dev)
+    value = R.aggregate_gbs(step_bytes, args.steps, ws, elapsed)
     clocks = clk.summary()
 
     # ---- roofline of the batch kernel (on-chip shared-memory lookup bound)
@@ -592,7 +596,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.requests == 4096 else f"{args.requests} requests of: " + WORKLOAD,
+            "config": {"workload": workload_name(args.requests),
                        "global_batch": args.requests * ws, "seq_len": None,
                        "parallelism": f"replicas{ws}", "step_bytes": step_bytes,
                        "l2": "no flush: 3.8 GB of inputs per step, far above the 129 MB L2",
@@ -732,12 +736,9 @@ def run_e2e(A, torch, w, ctxs, args, sh, stream, dist, ws):
     b.record(stream)
     stream.synchronize()
     secs = a.elapsed_time(b) / 1e3
-    if dist:
-        t = torch.tensor([secs], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+    secs = R.max_over_ranks(secs, dist, torch.device("cuda", torch.cuda.current_device()))
     plan.close()
-    return {"value": round(ws * nbytes * steps / secs / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+    return {"value": round(R.aggregate_gbs(nbytes, steps, ws, secs), 3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes, "steps": steps,
             "how": "aes_batch_plan_launch on pinned host buffers (zero-copy over NVLink-C2C)"}
 
