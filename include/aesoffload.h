@@ -136,7 +136,9 @@ typedef struct {
 /* Options of the persistent batch kernel (all-zero = tuned defaults). */
 typedef struct {
     int variant;        /* AES_VARIANT_* (AUTO picks T-table) */
-    int threads;        /* CTA size */
+    int threads;        /* CTA size, multiple of 32, 32..1024 (default 512): up
+                           to 512 the warps keep round keys in registers,
+                           above it in shared memory */
     int tile_blocks;    /* 16-byte blocks per work tile: a multiple of 256 (whole counter groups) */
     int ctas;           /* persistent CTAs; 0 = one per SM (x occupancy) */
     uint32_t tile_order_seed; /* nonzero: tiles are claimed in a seeded

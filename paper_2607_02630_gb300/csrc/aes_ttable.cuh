@@ -81,6 +81,23 @@ struct RkShared {
     __device__ __forceinline__ uint4 get(int r) const { return w[r]; }
 };
 
+// Round keys held in registers -- the batch kernel's warps, one request at a
+// time.  The schedule is read once per tile (NR + 1 uniform 16-byte loads);
+// indices are compile-time after unrolling, so every round's key is four
+// register operands and costs no shared-memory wavefront.  The price is
+// 4 * (NR + 1) registers a thread, which the 512-thread batch CTA can pay.
+template <int NR>
+struct RkRegs {
+    uint4 w[NR + 1];
+    __device__ __forceinline__ explicit RkRegs(const uint4 *__restrict__ g)
+    {
+#pragma unroll
+        for (int r = 0; r <= NR; ++r)
+            w[r] = __ldg(g + r);
+    }
+    __device__ __forceinline__ uint4 get(int r) const { return w[r]; }
+};
+
 // Rounds R0..NR-1 (full) and the final round NR on NB blocks held as
 // s[b][0..3] (little-endian column words), in place.  The state passed in is
 // the output of round R0 - 1.

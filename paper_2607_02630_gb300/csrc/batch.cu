@@ -7,9 +7,12 @@
 // the persistent CTAs (one per SM, T-tables filled once per CTA) each claim
 // tiles through one device atomic counter until none are left, so long and
 // short requests, AES-128 and AES-256, spread over all SMs (work stealing)
-// without any CTA-wide barrier per tile.  The round keys of a warp's current
-// tile are staged in that warp's slice of shared memory; the cipher is the
-// same T-table round code as the single-buffer kernel.
+// without any CTA-wide barrier per tile.  The cipher is the same T-table
+// round code as the single-buffer kernel.  Round keys: CTAs of up to 512
+// threads (the default) hold the current request's schedule in registers
+// (128 registers a thread), so the shared-memory pipe, the kernel's bound,
+// serves T-table lookups only; larger CTAs stage it in each warp's slice of
+// shared memory (one broadcast wavefront per round, about 5% of the pipe).
 //
 // A nonzero `order` enables a test aid: tile t is processed as tile
 // (a*t + b) mod T for a host-chosen a coprime to T (a permutation), so tiles
@@ -34,19 +37,22 @@ struct TileOrder {
     uint64_t a, b;  // t -> (a*t + b) mod T; a == 1, b == 0 is the identity
 };
 
-template <int NB>
-__global__ void __launch_bounds__(1024, 1)
+// CTA sizes up to this hold round keys in registers.
+constexpr int kRegsMaxThreads = 512;
+
+template <int NB, int MAXT, bool RK_REGS>
+__global__ void __launch_bounds__(MAXT, 1)
     batch_ttable_kernel(const BatchReq *__restrict__ reqs, const uint32_t *__restrict__ tile_req,
                         uint64_t total_tiles, unsigned long long *__restrict__ counter,
                         const uint32_t *__restrict__ te0, uint32_t tile_groups, TileOrder order)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint4 s_rk[32][15];  // round keys of each warp's current tile
+    __shared__ uint4 s_rk[RK_REGS ? 1 : MAXT / 32][15];  // round keys of each warp's current tile
     aestt::fill_tables(smem, te0);
     __syncthreads();
     const aestt::Lanes ln;
     const uint32_t lane = threadIdx.x & 31u;
-    uint4 *w_rk = s_rk[threadIdx.x >> 5];
+    uint4 *w_rk = s_rk[RK_REGS ? 0 : threadIdx.x >> 5];
     const bool permuted = order.a != 1 || order.b != 0;
     // Every warp claims tiles on its own: no CTA-wide barrier per tile.
     for (;;) {
@@ -59,12 +65,20 @@ __global__ void __launch_bounds__(1024, 1)
         if (permuted)
             t = (order.a * t + order.b) % total_tiles;
         const BatchReq rq = reqs[__ldg(tile_req + t)];
-        if (lane <= rq.nr)
-            w_rk[lane] = rq.rk[lane];
-        __syncwarp();
         uint64_t first, last;
         aestile::tile_blocks_of(t - rq.tile_begin, tile_groups, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first,
                                 &last);
+        if (RK_REGS) {
+            switch (rq.nr) {
+            case 10: aestile::run_tile_warp_regs<10, NB>(rq, first, last, smem, ln); break;
+            case 12: aestile::run_tile_warp_regs<12, NB>(rq, first, last, smem, ln); break;
+            default: aestile::run_tile_warp_regs<14, NB>(rq, first, last, smem, ln); break;
+            }
+            continue;
+        }
+        if (lane <= rq.nr)
+            w_rk[lane] = rq.rk[lane];
+        __syncwarp();
         switch (rq.nr) {
         case 10: aestile::run_tile_warp<10, NB>(rq, first, last, smem, ln, w_rk); break;
         case 12: aestile::run_tile_warp<12, NB>(rq, first, last, smem, ln, w_rk); break;
@@ -82,8 +96,12 @@ constexpr size_t kBatchSmem = aestt::kTableBytes;
 
 cudaError_t batch_set_attributes()
 {
-    return cudaFuncSetAttribute(batch_ttable_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kBatchSmem);
+    cudaError_t e = cudaFuncSetAttribute(batch_ttable_kernel<2, kRegsMaxThreads, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+    if (!e)
+        e = cudaFuncSetAttribute(batch_ttable_kernel<2, 1024, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kBatchSmem);
+    return e;
 }
 
 
@@ -235,8 +253,12 @@ cudaError_t launch_batch_image(uint8_t *img, const DeviceImage &im, const BatchT
     const uint32_t *map = reinterpret_cast<const uint32_t *>(img + im.off_map);
     unsigned long long *counter = reinterpret_cast<unsigned long long *>(img + im.off_counter);
     const uint32_t tg = (uint32_t)(s.tile_blocks / 256);
-    batch_ttable_kernel<2><<<ctas, s.threads, kBatchSmem, stream>>>(reqs, map, bt.total_tiles, counter, te0,
-                                                                     tg, order);
+    if (s.threads <= kRegsMaxThreads)
+        batch_ttable_kernel<2, kRegsMaxThreads, true>
+            <<<ctas, s.threads, kBatchSmem, stream>>>(reqs, map, bt.total_tiles, counter, te0, tg, order);
+    else
+        batch_ttable_kernel<2, 1024, false>
+            <<<ctas, s.threads, kBatchSmem, stream>>>(reqs, map, bt.total_tiles, counter, te0, tg, order);
     return cudaGetLastError();
 }
 

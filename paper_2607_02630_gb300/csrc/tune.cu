@@ -57,7 +57,7 @@ void tune_defaults(DeviceState &st)
     for (int i = 0; i < 3; ++i)
         for (int b = 0; b < kLenBuckets; ++b)
             st.ctr_tuned[i][b] = default_shape(st.nsm, b);
-    st.batch_tuned = BatchShape{AES_VARIANT_TTABLE, 1024, 1024, 0};
+    st.batch_tuned = BatchShape{AES_VARIANT_TTABLE, 512, 2048, 0};
 }
 
 CtrShape tuned_ctr_shape(const DeviceState &st, size_t len, int nr)

@@ -45,7 +45,8 @@ def mixed_lengths(g, k):
     return fixed + rand
 
 
-@pytest.mark.parametrize("tile_blocks,threads", [(1024, 1024), (2048, 1024), (8192, 1024), (512, 256), (4096, 512)])
+@pytest.mark.parametrize("tile_blocks,threads", [(1024, 1024), (2048, 512), (8192, 1024), (512, 256), (4096, 512),
+                                                 (1024, 544), (2048, 0)])
 def test_mixed_batch_matches_oracle(cuda, aes, ncpu, tile_blocks, threads):
     g = W.rng(40 + tile_blocks)
     lengths = mixed_lengths(g, 48)
