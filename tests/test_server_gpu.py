@@ -282,3 +282,46 @@ def test_open_loop_drivers_match_oracle(cuda, aes, path):
         o = int(offs[i])
         np.testing.assert_array_equal(out[o: o + n_i], oracle.ctr(key, bits, ivs[i], payload[o: o + n_i]),
                                       err_msg=f"request {i}")
+
+
+def test_zero_length_requests_with_slot_reuse(cuda, aes, ncpu):
+    """A zero-length request completes when the device reads it, so its slot
+    can be reused for a later request before the claim cursor reaches it.
+    Interleave zero-length requests (polled and their slots reused at once)
+    with real ones on a server with few slots: everything must complete and
+    the real requests must match the oracle."""
+    srv = aes.Server(slots=4, max_keys=2, ctas=16, idle_timeout_us=500_000)
+    try:
+        g = W.rng(66)
+        key = W.random_bytes(g, 16)
+        ks = srv.key_register(key.tobytes(), 128)
+        n_real, size = 48, 256 << 10
+        payload, offs, src, dst = arena(cuda, g, [size] * n_real)
+        ivs = [W.random_bytes(g, 16) for _ in range(n_real)]
+        pending = []
+        zeros = 0
+        for i in range(n_real):
+            while True:
+                rc, t = srv.submit_status(ks, ivs[i].tobytes(), src.data_ptr() + int(offs[i]),
+                                          dst.data_ptr() + int(offs[i]), size)
+                if rc == aes.AES_OK:
+                    break
+                assert rc == aes.AES_EAGAIN
+                assert srv.wait(pending.pop(0), WAIT_US) == aes.AES_OK
+            pending.append(t)
+            for _ in range(3):  # zero-length requests behind it, reaped at once
+                rc, tz = srv.submit_status(ks, ivs[i].tobytes(), src.data_ptr(), dst.data_ptr(), 0)
+                if rc == aes.AES_EAGAIN:
+                    continue
+                assert rc == aes.AES_OK
+                assert srv.wait(tz, WAIT_US) == aes.AES_OK
+                zeros += 1
+        for t in pending:
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+        assert zeros > 0
+        out = to_host(dst)
+        for i in range(n_real):
+            o = int(offs[i])
+            np.testing.assert_array_equal(out[o: o + size], oracle.ctr_mt(key, 128, ivs[i], payload[o: o + size], ncpu))
+    finally:
+        assert srv.close() == aes.AES_OK
