@@ -465,6 +465,47 @@ def served(args, rank, local):
     return 0
 
 
+def reroute_sweep(args, rank, local):
+    """The reroute block-size sweep: a single-event-loop asyncio server at 50
+    closed-loop clients (a spawned process, 127.0.0.1 TCP), per AES-128 block
+    size from 4 KiB to 256 MiB (the paper sweeps 4 KiB to 8 MiB): single-op
+    latency of the blocking offload, and
+    requests/s when the loop waits for the offload (sync), hands it to a
+    32-thread executor, or submits it to the served path and suspends."""
+    import torch
+
+    from paper_2607_02630_gb300 import aesoffload as A
+    from paper_2607_02630_gb300 import build as libbuild
+    from paper_2607_02630_gb300 import reroute as RR
+
+    torch.cuda.set_device(local)
+    libbuild.build()
+    A.lib()
+    dev = torch.device("cuda", local)
+    sizes = [int(x) for x in args.reroute_sizes.split(",")]
+    srv = A.Server(slots=256, max_keys=64, idle_timeout_us=5_000_000)
+    key = bytes(W.random_bytes(W.rng(W.SEED_BASE + 9), 16))
+    rows = []
+    try:
+        for i, n in enumerate(sizes):
+            row = RR.run_point(A, torch, dev, n, srv, key, 128, nclients=args.reroute_clients,
+                               seconds=args.reroute_seconds, warmup=0.5, executor_threads=32,
+                               seed=W.SEED_BASE + 10 + i)
+            row.pop("_outputs")
+            rows.append(row)
+            torch.cuda.empty_cache()
+    finally:
+        srv.close()
+    out = {"metric": "reroute on a single-event-loop server: req/s sync vs executor vs served, by block size",
+           "unit": "req/s", "rows": rows,
+           "config": {"server": "python asyncio, one event loop", "clients": args.reroute_clients,
+                      "executor_threads": 32, "cipher": "AES-128-CTR", "payload": "resident in HBM",
+                      "seconds_per_point": args.reroute_seconds}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------- our arm
 
 def main():
@@ -486,6 +527,11 @@ def main():
     ap.add_argument("--sweep-bits", default="128,256")
     ap.add_argument("--sweep-variants", default="ttable,bitslice")
     ap.add_argument("--sweep-reps", type=int, default=20)
+    ap.add_argument("--reroute", action="store_true",
+                    help="reroute block-size sweep on a single-event-loop server instead of the batch step")
+    ap.add_argument("--reroute-sizes", default=",".join(str(4096 << k) for k in range(17)))
+    ap.add_argument("--reroute-clients", type=int, default=50)
+    ap.add_argument("--reroute-seconds", type=float, default=2.0)
     ap.add_argument("--served", action="store_true",
                     help="served-mode studies: open-loop Poisson rates and the large 8 MiB stream")
     ap.add_argument("--served-requests", type=int, default=20000)
@@ -495,6 +541,8 @@ def main():
         return reference_arm(args, ws, rank)
     if args.sweep:
         return sweep(args, rank, local)
+    if args.reroute:
+        return reroute_sweep(args, rank, local)
     if args.served:
         return served(args, rank, local)
 

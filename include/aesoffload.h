@@ -116,6 +116,14 @@ typedef struct {
 int aes_ctr(aes_ctx_t ctx, const uint8_t *iv, const void *in, void *out, size_t len,
             void *stream);
 
+/* The blocking offload call a server makes on its own thread (the call
+ * Sec. 3's reroute moves off the event loop): aes_ctr on `stream`, then poll
+ * an event recorded behind it with cudaEventQuery until the work is done,
+ * the completion mechanism of the paper's GPU offload (Sec. 6 setup).  Same
+ * arguments and errors as aes_ctr, plus AES_ECUDA if the wait fails.  Uses
+ * one event per calling thread, created on first use. */
+int aes_ctr_sync(aes_ctx_t ctx, const uint8_t *iv, const void *in, void *out, size_t len, void *stream);
+
 /* aes_ctr with an explicit launch shape (autotuner, tests, sweeps); `cfg`
  * NULL behaves like aes_ctr.  Extra error: AES_EINVAL for a shape outside the
  * documented ranges. */
@@ -258,6 +266,15 @@ int offload_submit(offload_server_t srv, int key_slot, const uint8_t *iv, const 
  * AES_EINVAL), AES_PENDING while in flight, AES_EDESC if the device rejected
  * the descriptor, AES_EINVAL for an unknown ticket.  Thread-safe. */
 int offload_poll(offload_server_t srv, uint64_t ticket);
+
+/* Completion wait over many tickets, for a server's completion thread
+ * (the resume step of Sec. 3 for a batch of suspended requests): poll every
+ * ticket until at least one is no longer pending or `timeout_us` passes.
+ * status[i] receives offload_poll's result for tickets[i] (AES_PENDING for
+ * those still in flight; a finished ticket is released exactly as by
+ * offload_poll).  Returns the number of tickets no longer pending, 0 on
+ * timeout, AES_EINVAL for bad arguments.  n == 0 returns 0 at once. */
+int offload_poll_many(offload_server_t srv, const uint64_t *tickets, int n, int *status, uint64_t timeout_us);
 
 /* Poll until done or `timeout_us` passes (AES_ETIMEOUT, ticket stays live). */
 int offload_wait(offload_server_t srv, uint64_t ticket, uint64_t timeout_us);

@@ -89,6 +89,8 @@ _SIGS = {
     "aes_ctx_round_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "aes_ctr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_size_t, ctypes.c_void_p]),
+    "aes_ctr_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p]),
     "aes_ctr_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(LaunchShape)]),
     "aes_ctr_batch": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int, ctypes.c_void_p]),
@@ -109,6 +111,8 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]),
     "offload_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "offload_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]),
+    "offload_poll_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_uint64]),
     "offload_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "offload_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "offload_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -229,6 +233,13 @@ def ctr(ctx: Context, iv, src, dst, nbytes: int | None = None, stream=None, **sh
     _check(ctr_status(ctx, iv, src, dst, nbytes, stream, **shape), "aes_ctr")
 
 
+def ctr_sync(ctx: Context, iv, src, dst, nbytes: int, stream=None) -> None:
+    """The blocking offload call: aes_ctr, then poll its completion event
+    (aes_ctr_sync; the GIL is released for the whole call)."""
+    _check(lib().aes_ctr_sync(ctx.handle, _bytes16(iv), ptr(src), ptr(dst), int(nbytes), stream_handle(stream)),
+           "aes_ctr_sync")
+
+
 def _descs(requests):
     arr = (Desc * max(len(requests), 1))()
     for i, (ctx, iv, src, dst, n) in enumerate(requests):
@@ -328,6 +339,18 @@ class Server:
 
     def poll(self, ticket: int) -> int:
         return lib().offload_poll(self.handle, ctypes.c_uint64(ticket))
+
+    def poll_many(self, tickets, timeout_us: int = 1000):
+        """offload_poll_many over a sequence of tickets: (number done, status
+        per ticket); the GIL is released while it waits."""
+        import numpy as np
+
+        t = np.ascontiguousarray(np.asarray(tickets, dtype=np.uint64))
+        st = np.empty(t.size, dtype=np.int32)
+        rc = lib().offload_poll_many(self.handle, t.ctypes.data, int(t.size), st.ctypes.data, int(timeout_us))
+        if rc < 0:
+            raise AesError(rc, "offload_poll_many")
+        return rc, st
 
     def wait(self, ticket: int, timeout_us: int = 5_000_000) -> int:
         return lib().offload_wait(self.handle, ctypes.c_uint64(ticket), ctypes.c_uint64(timeout_us))

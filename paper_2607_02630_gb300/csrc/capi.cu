@@ -309,4 +309,43 @@ int aes_ctr(aes_ctx_t ctx, const uint8_t *iv, const void *in, void *out, size_t 
     return aes_ctr_ex(ctx, iv, in, out, len, stream, nullptr);
 }
 
+int aes_ctr_sync(aes_ctx_t ctx, const uint8_t *iv, const void *in, void *out, size_t len, void *stream)
+{
+    int rc = aes_ctr_ex(ctx, iv, in, out, len, stream, nullptr);
+    if (rc)
+        return rc;
+    // one completion event per host thread and device, reused across calls
+    struct ThreadEvent {
+        int device = -1;
+        cudaEvent_t ev = nullptr;
+        ~ThreadEvent()
+        {
+            if (ev)
+                cudaEventDestroy(ev);
+        }
+    };
+    thread_local ThreadEvent te;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e && (te.device != dev || !te.ev)) {
+        if (te.ev)
+            cudaEventDestroy(te.ev);
+        te.ev = nullptr;
+        e = cudaEventCreateWithFlags(&te.ev, cudaEventDisableTiming);
+        te.device = e ? -1 : dev;
+    }
+    if (!e)
+        e = cudaEventRecord(te.ev, static_cast<cudaStream_t>(stream));
+    while (!e) {
+        e = cudaEventQuery(te.ev);
+        if (e == cudaErrorNotReady)
+            e = cudaSuccess;
+        else
+            break;
+    }
+    if (e)
+        return cuda_fail(e, "aes_ctr_sync");
+    return AES_OK;
+}
+
 }  // extern "C"

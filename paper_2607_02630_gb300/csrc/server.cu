@@ -881,6 +881,26 @@ int offload_poll(offload_server_t s, uint64_t ticket)
     return AES_OK;
 }
 
+int offload_poll_many(offload_server_t s, const uint64_t *tickets, int n, int *status, uint64_t timeout_us)
+{
+    if (!s || n < 0 || (n > 0 && (!tickets || !status)))
+        return AES_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        int done = 0;
+        for (int i = 0; i < n; ++i) {
+            status[i] = offload_poll(s, tickets[i]);
+            done += status[i] != AES_PENDING;
+        }
+        if (done || n == 0)
+            return done;
+        const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
+        if ((uint64_t)us >= timeout_us)
+            return 0;
+    }
+}
+
 int offload_wait(offload_server_t s, uint64_t ticket, uint64_t timeout_us)
 {
     const auto t0 = std::chrono::steady_clock::now();

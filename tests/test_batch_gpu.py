@@ -148,3 +148,37 @@ def test_full_size_batch_workload_sampled(cuda, aes, ncpu):
             np.testing.assert_array_equal(to_host(dst[o + start: o + end]), want,
                                           err_msg=f"request {i} window {start}")
     plan.close()
+
+
+def test_batch_pinned_host_buffers(cuda, aes, ncpu):
+    """Batch requests whose payloads live in pinned host memory (the kernel
+    reads and writes them over NVLink-C2C through their device aliases), mixed
+    with device-resident ones in the same launch."""
+    g = W.rng(48)
+    lengths = [1, 17, 4096 + 5, 1 << 20, (1 << 20) + 9, 3 << 16]
+    pad = [(n + 255) // 256 * 256 + 256 for n in lengths]
+    offs = np.concatenate([[0], np.cumsum(pad)[:-1]]).astype(np.int64)
+    total = int(sum(pad))
+    payload = W.random_bytes(g, total)
+    hsrc = cuda.from_numpy(payload.copy()).pin_memory()
+    hdst = cuda.full((total,), 0xA5, dtype=cuda.uint8).pin_memory()
+    dsrc = to_dev(cuda, payload)
+    ddst = to_dev(cuda, np.zeros(0, np.uint8), pad=total)
+    reqs, meta = [], []
+    for i, n in enumerate(lengths):
+        bits = (128, 256)[i % 2]
+        key = W.random_bytes(g, bits // 8)
+        iv = iv_with_low(g, ("random", "low32")[i % 2])
+        ctx = aes.Context(key.tobytes(), bits)
+        o = int(offs[i])
+        src, dst = (hsrc, hdst) if i % 3 != 2 else (dsrc, ddst)
+        reqs.append((ctx, iv.tobytes(), src.data_ptr() + o, dst.data_ptr() + o, n))
+        meta.append((key, bits, iv, o, n, i % 3 != 2))
+    aes.batch(reqs)
+    cuda.cuda.synchronize()
+    hout, dout = hdst.numpy(), to_host(ddst)
+    for key, bits, iv, o, n, on_host in meta:
+        out = hout if on_host else dout
+        want = oracle.ctr_mt(key, bits, iv, payload[o: o + n], ncpu)
+        np.testing.assert_array_equal(out[o: o + n], want, err_msg=f"request at {o} len {n}")
+        assert (out[o + n: o + n + 16] == 0xA5).all(), "bytes past len were written"

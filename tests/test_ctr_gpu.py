@@ -198,3 +198,21 @@ def test_autotune_then_auto_shapes_stay_exact(cuda, aes, ncpu, tmp_path):
         data = W.random_bytes(g, n)
         np.testing.assert_array_equal(gpu_ctr(cuda, aes, ctx, iv, data),
                                       oracle.ctr_mt(key, 256, iv, data, ncpu))
+
+
+def test_ctr_sync_blocks_until_done(cuda, aes, ncpu):
+    """aes_ctr_sync returns only once the output is complete: read it without
+    any device synchronisation."""
+    g = W.rng(34)
+    key = W.random_bytes(g, 32)
+    ctx = aes.Context(key.tobytes(), 256)
+    data = W.random_bytes(g, (1 << 20) + 5)
+    iv = W.random_bytes(g, 16)
+    src = cuda.from_numpy(data).pin_memory()
+    dst = cuda.zeros(data.size, dtype=cuda.uint8).pin_memory()
+    s = cuda.cuda.Stream()
+    for _ in range(3):
+        dst.zero_()
+        aes.ctr_sync(ctx, iv.tobytes(), src, dst, data.size, stream=s)
+        np.testing.assert_array_equal(dst.numpy(), oracle.ctr_mt(key, 256, iv, data, ncpu))
+    assert aes.lib().aes_ctr_sync(None, iv.tobytes(), src.data_ptr(), dst.data_ptr(), 16, 0) == aes.AES_EINVAL

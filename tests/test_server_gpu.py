@@ -325,3 +325,66 @@ def test_zero_length_requests_with_slot_reuse(cuda, aes, ncpu):
             np.testing.assert_array_equal(out[o: o + size], oracle.ctr_mt(key, 128, ivs[i], payload[o: o + size], ncpu))
     finally:
         assert srv.close() == aes.AES_OK
+
+
+def test_served_pinned_host_buffers(cuda, aes, ncpu):
+    """Served requests whose input and output live in pinned host memory: the
+    resident kernel writes the output over NVLink-C2C and orders it at system
+    scope before raising the completion flag the host polls."""
+    srv = aes.Server(slots=16, max_keys=2, ctas=16, idle_timeout_us=500_000)
+    try:
+        g = W.rng(67)
+        key = W.random_bytes(g, 32)
+        ks = srv.key_register(key.tobytes(), 256)
+        sizes = [16, 4096 + 3, 1 << 20, (1 << 20) + 1, 2 << 20]
+        pad = [(n + 255) // 256 * 256 + 256 for n in sizes]
+        offs = np.concatenate([[0], np.cumsum(pad)[:-1]]).astype(np.int64)
+        total = int(sum(pad))
+        payload = W.random_bytes(g, total)
+        hsrc = cuda.from_numpy(payload.copy()).pin_memory()
+        hdst = cuda.full((total,), 0xA5, dtype=cuda.uint8).pin_memory()
+        ivs = [W.random_bytes(g, 16) for _ in sizes]
+        tickets = [srv.submit(ks, ivs[i].tobytes(), hsrc.data_ptr() + int(offs[i]), hdst.data_ptr() + int(offs[i]),
+                              n) for i, n in enumerate(sizes)]
+        for t in tickets:
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+        out = hdst.numpy()  # no device synchronisation: the completion flag orders the output
+        for i, n in enumerate(sizes):
+            o = int(offs[i])
+            np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, 256, ivs[i], payload[o: o + n], ncpu))
+            assert (out[o + n: o + n + 16] == 0xA5).all()
+    finally:
+        assert srv.close() == aes.AES_OK
+
+
+def test_poll_many(cuda, aes, ncpu):
+    """offload_poll_many reports finished tickets (and releases them) and
+    times out with 0 when nothing is done."""
+    srv = aes.Server(slots=16, max_keys=2, ctas=16, idle_timeout_us=500_000)
+    try:
+        g = W.rng(68)
+        key = W.random_bytes(g, 16)
+        ks = srv.key_register(key.tobytes(), 128)
+        sizes = [4096, 1 << 20, 16, 3 << 18]
+        payload, offs, src, dst = arena(cuda, g, sizes)
+        ivs = [W.random_bytes(g, 16) for _ in sizes]
+        pending = {srv.submit(ks, ivs[i].tobytes(), src.data_ptr() + int(offs[i]), dst.data_ptr() + int(offs[i]), n): i
+                   for i, n in enumerate(sizes)}
+        deadline = time.time() + 10
+        while pending and time.time() < deadline:
+            tickets = list(pending)
+            n, st = srv.poll_many(tickets, 100_000)
+            assert n == int((st != aes.AES_PENDING).sum())
+            for t, rc in zip(tickets, st.tolist()):
+                if rc != aes.AES_PENDING:
+                    assert rc == aes.AES_OK
+                    assert srv.poll(t) == aes.AES_EINVAL  # released
+                    del pending[t]
+        assert not pending
+        assert srv.poll_many([], 0)[0] == 0
+        out = to_host(dst)
+        for i, n in enumerate(sizes):
+            o = int(offs[i])
+            np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, 128, ivs[i], payload[o: o + n], ncpu))
+    finally:
+        assert srv.close() == aes.AES_OK
