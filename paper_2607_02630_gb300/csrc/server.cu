@@ -21,22 +21,28 @@
 //   cursor     seq (28 bits) | slot d (16 bits) | next tile (20 bits) of the request
 //              being cut into tiles; tiles are claimed with atomicAdd
 //   adv        sequence number an elected CTA is advancing the cursor to
+//   disp       next sequence number to dispatch (validate into recs)
+//   disp_ring  (seq, slot, tile count) of the last 64 dispatched requests,
+//              written once their records are complete
 //   recs[d]    validated copy of the request in slot d, its tile count and a count of
 //              finished tiles
 //
 // Each resident CTA is warp-specialised: warp 0 is the agent, the others are
 // workers.  The agent alone touches the global cursor: it claims tiles in
-// batches (as many as its workers are waiting for, plus a small prefetch) and
-// hands them to the workers through a ring in shared memory; when the current
-// request has no tiles left it either becomes the elected advancer (reads the
-// next queue entry, validates it into recs[d], moves the cursor) or waits for
-// the CTA that is.  A tile is tile_groups counter groups of one request and is
-// encrypted by one worker warp, so a request is spread over many SMs at once
-// and requests that arrive while others are on the GPU start as soon as an
-// agent asks for work (continuous batching).  Every wait on the device is
-// bounded: an agent with no new work for idle_timeout exits and its workers
-// follow once the ring is drained (the host relaunches the kernel on the
-// next submit or poll), and the stop flag ends every wait.
+// batches (as many as its workers are waiting for, plus a prefetch) and hands
+// them to the workers through a ring in shared memory.  Requests are
+// dispatched ahead of the cursor, in order, up to 4 per round trip over the
+// host link (tags read together, claimed with one CAS on disp).  When a claim
+// takes a request's last tiles, or a claim finds none left, that agent (one,
+// elected through adv) moves the cursor to the next request as soon as its
+// dispatch-ring entry is published, and dispatches what is queued behind it.
+// A tile is tile_groups counter groups of one request and is encrypted by one
+// worker warp, so a request is spread over many SMs at once and requests that
+// arrive while others are on the GPU start as soon as an agent asks for work
+// (continuous batching).  Every wait on the device is bounded: an agent with
+// no new work for idle_timeout exits and its workers follow once the ring is
+// drained (the host relaunches the kernel on the next submit or poll), and
+// the stop flag ends every wait.
 #include "../../include/aesoffload.h"
 #include "internal.h"
 #include "runtime.h"
@@ -62,6 +68,7 @@ constexpr uint32_t kTileMask = (1u << kTileBits) - 1;
 constexpr uint32_t kMaxTiles = (1u << kTileBits) - 16384;  // headroom for batched exhausted claims
 constexpr int kMaxSlots = 65535;
 constexpr uint32_t kExitStop = 1, kExitIdle = 2, kExitError = 4;
+constexpr uint32_t kNotReady = 8;  // advance(): next request not ready (not an exit reason)
 constexpr int kMaxWarps = 24;   // CTA of at most 768 threads (80 registers each)
 constexpr uint32_t kRing = 64;  // >= workers + prefetch
 // Tiles an agent keeps queued for its workers.  A deep queue rides through
@@ -71,6 +78,7 @@ constexpr uint32_t kPrefetch = 16;
 constexpr uint32_t kMaxClaim = 4;    // tiles per claim: spreads a request over many SMs
 constexpr uint32_t kLookahead = 8;   // requests validated ahead of the cursor
 constexpr uint32_t kDispRing = 64;   // > kLookahead
+constexpr uint32_t kDispatchBatch = 4;  // queue entries read per round trip over the host link
 
 struct QEntry {  // 64 bytes, host-written, tag last
     uint64_t tag;  // sequence number + 1
@@ -97,8 +105,7 @@ struct SrvParams {
     unsigned long long *cursor;
     unsigned long long *adv;
     unsigned long long *disp;      // next sequence number to dispatch (validate into recs)
-    unsigned int *disp_slot;       // kDispRing: (s & 0xffff) << 16 | slot d of dispatched sequence number
-                                   // s, at s % kDispRing (d = 0xffff: an entry the host never writes)
+    unsigned long long *disp_ring; // kDispRing: ring_entry() of dispatched request s at s % kDispRing
     SrvRec *recs;
     const uint4 *keys;          // max_keys x 15 round keys
     const int *key_nr;          // max_keys; 0 = unregistered
@@ -116,12 +123,6 @@ __device__ __forceinline__ uint64_t gtime()
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-__device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t *p)
-{
-    uint64_t v;
-    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
 }
 __device__ __forceinline__ void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
 {
@@ -160,168 +161,205 @@ struct StopCheck {
     }
 };
 
-// Dispatch request k if its queue entry is present and nobody else has:
-// validate it into recs[d] (the tile count and sequence number last) and
-// note its slot in disp_slot.  Requests are dispatched in sequence order, one
-// dispatcher per request (the CAS on disp), and only ahead of the cursor.
-// Returns true if this thread dispatched k.
-__device__ bool try_dispatch(const SrvParams &p, uint32_t k, uint32_t *slot = nullptr)
+// Entry of the dispatch ring for request k: sequence number (28 bits), slot
+// d (16 bits; 0xffff marks a queue entry the host never writes) and tile
+// count (20 bits).  It is stored after the request's record is complete, so
+// an entry that carries k is all the advancer needs to move the cursor.
+__device__ __forceinline__ uint64_t ring_entry(uint32_t k, uint32_t d, uint32_t ntiles)
 {
-    const QEntry *q = p.queue + (k & p.qmask);
-    const uint64_t tag = ld_acquire_sys(&q->tag);
-    if ((uint32_t)(tag & kSeqMask) != ((k + 1) & kSeqMask))
-        return false;  // not submitted yet
-    if (atomicCAS(p.disp, (unsigned long long)k, (unsigned long long)((k + 1) & kSeqMask)) != k)
-        return false;  // someone else dispatches it
-    // the rest of the entry, after the acquire of its tag: four independent 16-byte loads
-    const uint64_t *e = reinterpret_cast<const uint64_t *>(q);
-    uint64_t x1, x2, x3, x4, x5, x6, x7, unused;
-    ld_volatile_v2(e + 0, unused, x1);
-    ld_volatile_v2(e + 2, x2, x3);
-    ld_volatile_v2(e + 4, x4, x5);
-    ld_volatile_v2(e + 6, x6, x7);
-    (void)unused;
-    const uint64_t in = x1, out = x2, len = x3, iv_hi = x4, iv_lo = x5, gen = x6;
-    const uint32_t ks = (uint32_t)x7;
-    const uint32_t d = (uint32_t)(x7 >> 32) & 0xffffu;
-    const uint32_t flags = (uint32_t)(x7 >> 48);
-    if (d >= p.nslots) {  // the host never writes such an entry; the advancer stops on it
-        *reinterpret_cast<volatile unsigned int *>(p.disp_slot + (k % kDispRing)) = ((k & 0xffffu) << 16) | 0xffffu;
-        if (slot)
-            *slot = 0xffffffffu;
-        return true;
-    }
-    int nr = 0;
-    if (ks < p.max_keys)
-        nr = __ldcg(p.key_nr + ks);
-    bool ok = (nr == 10 || nr == 12 || nr == 14) && len <= p.max_len;
-    if (ok && len)
-        ok = in && out && !((in | out) & 15u);
-    uint32_t ntiles = 0, tg = 1, tp = 1;
-    if (ok && len) {
-        // tiles are runs of tg whole 256-block counter groups, or (tp > 1)
-        // equal parts of one group.  Unless fixed by the server config, a
-        // request is cut into about 512 tiles of 64..1024 blocks: short
-        // requests spread over many warps, long ones keep claims rare.
-        const uint64_t nb = (len + 15) >> 4;
-        const uint64_t groups = (((iv_lo & 255u) + nb - 1) >> 8) + 1;
-        uint32_t tb = p.tile_blocks;
-        if (!tb) {
-            tb = 64;
-            while (tb < 1024 && (uint64_t)tb * 512 < nb)
-                tb <<= 1;
-        }
-        if (tb >= 256)
-            tg = tb / 256;
-        else
-            tp = 256 / tb;
-        ntiles = (uint32_t)((groups + tg - 1) / tg * tp);
-    }
-    SrvRec *rec = p.recs + d;
-    rec->rq.in = reinterpret_cast<const uint4 *>(in);
-    rec->rq.out = reinterpret_cast<uint4 *>(out);
-    rec->rq.len = len;
-    rec->rq.iv_hi = iv_hi;
-    rec->rq.iv_lo = iv_lo;
-    rec->rq.rk = p.keys + 15u * (ok ? ks : 0u);
-    rec->rq.nr = (uint32_t)nr;
-    rec->rq.pad = flags;
-    rec->gen = gen;
-    rec->done_tiles = 0;
-    rec->tile_groups = tg;
-    rec->tile_parts = tp;
-    *reinterpret_cast<volatile unsigned int *>(p.disp_slot + (k % kDispRing)) = ((k & 0xffffu) << 16) | d;
-    __threadfence();
-    st_relaxed_gpu(&rec->seq_ntiles, ((uint64_t)k << kTileBits) | ntiles);
-    if (slot)
-        *slot = d;
-    if (ntiles == 0) {
-        __threadfence_system();
-        st_release_sys(p.done + d, (gen << 2) | (ok ? 1u : 2u));
-    }
-    return true;
+    return ((uint64_t)k << 36) | ((uint64_t)d << kTileBits) | ntiles;
 }
 
-// a is a later sequence number than b (28-bit wrap-around)
-__device__ __forceinline__ bool seq_after(uint32_t a, uint32_t b)
+__device__ __forceinline__ uint64_t ld_relaxed_sys(const uint64_t *p)
 {
-    const uint32_t d = (a - b) & kSeqMask;
-    return d != 0 && d < (1u << 27);
+    uint64_t v;
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Elected advancer: move the cursor from request seq to request seq + 1 once
-// that request is dispatched (dispatching it here if nobody has), then
-// dispatch what is already queued behind it, up to kLookahead ahead.
-// Returns 0 or an exit code (after handing the advancer role back).
-__device__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_work, StopCheck &stop)
+// Dispatch, in sequence order, up to n_max requests starting at k0 (the
+// value of disp the caller saw) whose queue entries are present: their tags
+// are read in one round trip over the host link and the requests claimed
+// with one CAS on disp (one dispatcher per request); then the entries are
+// read (acquire pattern: relaxed tag loads, then a system-scope fence) and
+// validated into recs[d], and finally their dispatch-ring entries are
+// published.  A request without tiles is completed here.  Returns the number
+// of requests dispatched (0: k0 not queued yet, or someone else took it) and,
+// in *first, the ring entry of request k0.
+__device__ __noinline__ uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, uint64_t *first = nullptr)
 {
-    const uint32_t nseq = (seq + 1) & kSeqMask;
-    uint32_t d = 0;
-    for (;;) {
-        const uint32_t dsp = (uint32_t)ld_relaxed_gpu(p.disp);
-        if (dsp == nseq) {
-            // not dispatched yet: do it if it is queued (then its slot is known)
-            if (try_dispatch(p, nseq, &d)) {
-                if (d >= p.nslots)
-                    return kExitError;
-                break;
-            }
-        } else {
-            const uint32_t e =
-                *reinterpret_cast<const volatile unsigned int *>(p.disp_slot + (nseq % kDispRing));
-            if ((e >> 16) == (nseq & 0xffffu)) {  // else its dispatcher has not written it yet
-                d = e & 0xffffu;
-                if (d >= p.nslots)
-                    return kExitError;
-                const uint32_t s2 = (uint32_t)(ld_relaxed_gpu(&p.recs[d].seq_ntiles) >> kTileBits);
-                if (s2 == nseq)
-                    break;  // dispatched and fully written
-                if (seq_after(s2, nseq)) {
-                    // A request with no tiles completes at dispatch, so the
-                    // host may have reused its slot for a later request
-                    // before the cursor got here: nothing is left to claim.
-                    d = 0xffffu;
-                    break;
-                }
-            }
+    uint32_t m = 0;
+    {
+        uint64_t tag[kDispatchBatch];
+#pragma unroll
+        for (uint32_t i = 0; i < kDispatchBatch; ++i)
+            tag[i] = i < n_max ? ld_relaxed_sys(&p.queue[(k0 + i) & p.qmask].tag) : 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kDispatchBatch; ++i)
+            if (m == i && i < n_max && (uint32_t)(tag[i] & kSeqMask) == ((k0 + i + 1) & kSeqMask))
+                m = i + 1;
+    }
+    if (m == 0)
+        return 0;
+    asm volatile("fence.acq_rel.sys;" ::: "memory");
+    if (atomicCAS(p.disp, (unsigned long long)k0, (unsigned long long)((k0 + m) & kSeqMask)) != k0)
+        return 0;
+    uint64_t x[kDispatchBatch][7];
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+        if (i < m) {
+            const uint64_t *e = reinterpret_cast<const uint64_t *>(p.queue + ((k0 + i) & p.qmask));
+            uint64_t unused;
+            ld_volatile_v2(e + 0, unused, x[i][0]);
+            ld_volatile_v2(e + 2, x[i][1], x[i][2]);
+            ld_volatile_v2(e + 4, x[i][3], x[i][4]);
+            ld_volatile_v2(e + 6, x[i][5], x[i][6]);
+            (void)unused;
         }
-        uint32_t r = 0;
-        if (stop(p.stop))
-            r = kExitStop;
-        else if (gtime() - last_work > p.idle_ns)
-            r = kExitIdle;
-        if (r) {
-            atomicCAS(p.adv, (unsigned long long)nseq, (unsigned long long)seq);
-            return r;
+    }
+    uint64_t ent[kDispatchBatch] = {};
+    uint32_t done_word[kDispatchBatch] = {};  // status for a request completed here, else 0
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+        if (i >= m)
+            continue;
+        const uint32_t k = (k0 + i) & kSeqMask;
+        const uint64_t in = x[i][0], out = x[i][1], len = x[i][2], iv_hi = x[i][3], iv_lo = x[i][4];
+        const uint32_t ks = (uint32_t)x[i][6];
+        const uint32_t d = (uint32_t)(x[i][6] >> 32) & 0xffffu;
+        const uint32_t flags = (uint32_t)(x[i][6] >> 48);
+        done_word[i] = 0;
+        if (d >= p.nslots) {  // the host never writes such an entry; the advancer stops on it
+            ent[i] = ring_entry(k, 0xffffu, 0);
+            continue;
         }
-        __nanosleep(32);
+        int nr = 0;
+        if (ks < p.max_keys)
+            nr = __ldcg(p.key_nr + ks);
+        bool ok = (nr == 10 || nr == 12 || nr == 14) && len <= p.max_len;
+        if (ok && len)
+            ok = in && out && !((in | out) & 15u);
+        uint32_t ntiles = 0, tg = 1, tp = 1;
+        if (ok && len) {
+            // tiles are runs of tg whole 256-block counter groups, or (tp > 1)
+            // equal parts of one group.  Unless fixed by the server config, a
+            // request is cut into about 512 tiles of 64..1024 blocks: short
+            // requests spread over many warps, long ones keep claims rare.
+            const uint64_t nb = (len + 15) >> 4;
+            const uint64_t groups = (((iv_lo & 255u) + nb - 1) >> 8) + 1;
+            uint32_t tb = p.tile_blocks;
+            if (!tb) {
+                tb = 64;
+                while (tb < 1024 && (uint64_t)tb * 512 < nb)
+                    tb <<= 1;
+            }
+            if (tb >= 256)
+                tg = tb / 256;
+            else
+                tp = 256 / tb;
+            ntiles = (uint32_t)((groups + tg - 1) / tg * tp);
+        }
+        SrvRec *rec = p.recs + d;
+        rec->rq.in = reinterpret_cast<const uint4 *>(in);
+        rec->rq.out = reinterpret_cast<uint4 *>(out);
+        rec->rq.len = len;
+        rec->rq.iv_hi = iv_hi;
+        rec->rq.iv_lo = iv_lo;
+        rec->rq.rk = p.keys + 15u * (ok ? ks : 0u);
+        rec->rq.nr = (uint32_t)nr;
+        rec->rq.pad = flags;
+        rec->gen = x[i][5];
+        rec->done_tiles = 0;
+        rec->tile_groups = tg;
+        rec->tile_parts = tp;
+        ent[i] = ring_entry(k, d, ntiles);
+        if (ntiles == 0)
+            done_word[i] = ok ? 1u : 2u;
     }
     __threadfence();
-    unsigned long long cur = ld_relaxed_gpu(p.cursor);
-    const unsigned long long nv = ((unsigned long long)nseq << 36) | ((unsigned long long)d << kTileBits);
-    for (uint32_t it = 0;; ++it) {
-        if ((uint32_t)(cur >> 36) != seq || it > (1u << 24))
-            return kExitError;  // only the elected advancer moves the sequence number
-        const unsigned long long old = atomicCAS(p.cursor, cur, nv);
-        if (old == cur)
-            break;
-        cur = old;
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+        const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
+        if (i < m && d != 0xffffu)
+            st_relaxed_gpu(&p.recs[d].seq_ntiles, ((ent[i] >> 36) << kTileBits) | (ent[i] & kTileMask));
     }
-    last_work = gtime();
-    // look ahead: validate requests already queued behind the new one
+    __threadfence();
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i)
+        if (i < m)
+            st_relaxed_gpu(p.disp_ring + ((k0 + i) % kDispRing), ent[i]);
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+        if (i < m && done_word[i]) {
+            const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
+            __threadfence_system();
+            st_release_sys(p.done + d, (x[i][5] << 2) | done_word[i]);
+        }
+    }
+    if (first)
+        *first = ent[0];
+    return m;
+}
+
+// Elected advancer (adv has been moved from seq to seq + 1): move the cursor
+// to request seq + 1 once its dispatch-ring entry is published (dispatching
+// it, with what is queued behind it, if it is next in line), step over
+// requests without tiles, and dispatch up to kLookahead requests ahead.
+// With block == false the role is handed back at once (kNotReady) when the
+// next request is not ready.  Returns 0, kNotReady or an exit code (after
+// handing the role back).
+__device__ __noinline__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_work, StopCheck &stop,
+                                        bool block)
+{
     for (;;) {
+        const uint32_t nseq = (seq + 1) & kSeqMask;
+        uint64_t e = 0;
+        for (;;) {
+            e = ld_relaxed_gpu(p.disp_ring + (nseq % kDispRing));
+            if ((uint32_t)(e >> 36) == nseq)
+                break;  // dispatched and published
+            const uint32_t dsp = (uint32_t)ld_relaxed_gpu(p.disp);
+            if (dsp == nseq && dispatch(p, nseq, kLookahead + 1, &e))
+                break;  // dispatched it here: e is its ring entry
+            uint32_t r = 0;
+            if (!block)
+                r = kNotReady;
+            else if (stop(p.stop))
+                r = kExitStop;
+            else if (gtime() - last_work > p.idle_ns)
+                r = kExitIdle;
+            if (r) {
+                atomicCAS(p.adv, (unsigned long long)nseq, (unsigned long long)seq);
+                return r;
+            }
+            __nanosleep(32);
+        }
+        const uint32_t d = (uint32_t)(e >> kTileBits) & 0xffffu;
+        if (d >= p.nslots)
+            return kExitError;
+        // Only the elected advancer changes the sequence number; claims that
+        // raced with it only added to the tile count of the old request.
+        atomicExch(p.cursor, ((unsigned long long)nseq << 36) | ((unsigned long long)d << kTileBits));
+        last_work = gtime();
         const uint32_t k = (uint32_t)ld_relaxed_gpu(p.disp);
-        if (((k - nseq) & kSeqMask) > kLookahead || !try_dispatch(p, k))
-            break;
+        const uint32_t ahead = (k - nseq) & kSeqMask;
+        if (ahead <= kLookahead)
+            dispatch(p, k, kLookahead + 1 - ahead);
+        if (e & kTileMask)
+            return 0;
+        // nothing to claim in nseq: step over it, unless another agent
+        // (which saw the empty request) already took that role
+        if (atomicCAS(p.adv, (unsigned long long)nseq, (unsigned long long)((nseq + 1) & kSeqMask)) != nseq)
+            return 0;
+        seq = nseq;
     }
-    return 0;
 }
 
 // Claim up to `want` tiles of the current request (the agent of a CTA).
 // Returns 0 with the tiles [*t0, *t1) of slot *d and its sequence number, or
 // an exit code.
 __device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &stop, uint32_t want,
-                          uint32_t *d_out, uint32_t *seq_out, uint32_t *t0, uint32_t *t1)
+                          uint32_t *d_out, uint32_t *seq_out, uint32_t *t0, uint32_t *t1, uint32_t *nt_out)
 {
     for (;;) {
         if (stop(p.stop))
@@ -338,6 +376,7 @@ __device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &st
                 *seq_out = seq;
                 *t0 = t;
                 *t1 = t + want < nt ? t + want : nt;
+                *nt_out = nt;
                 last_work = gtime();
                 return 0;
             }
@@ -345,7 +384,7 @@ __device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &st
         // The current request has no tiles left: advance, or wait for the
         // CTA that does.
         if (atomicCAS(p.adv, (unsigned long long)seq, (unsigned long long)((seq + 1) & kSeqMask)) == seq) {
-            const uint32_t r = advance(p, seq, last_work, stop);
+            const uint32_t r = advance(p, seq, last_work, stop, true);
             if (r)
                 return r;
         } else {
@@ -378,6 +417,7 @@ __device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
     uint64_t last_work = gtime();
     StopCheck stop;
     uint32_t ld = 0, lseq = 0, lt = 0, lend = 0;  // current lease: tiles [lt, lend) of slot ld
+    bool adv_after = false;                      // the lease ends its request
     uint32_t code = 0;
     uint32_t backoff = 32;  // ns; a spinning agent would take shared-memory cycles from its workers
     for (;;) {
@@ -398,9 +438,11 @@ __device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
         if (lt >= lend) {
             const uint32_t waiting = (int32_t)(head - tail) > 0 ? head - tail : 0u;
             const uint32_t want = waiting + kPrefetch < kMaxClaim ? waiting + kPrefetch : kMaxClaim;
-            code = claim(p, last_work, stop, want, &ld, &lseq, &lt, &lend);
+            uint32_t nt = 0;
+            code = claim(p, last_work, stop, want, &ld, &lseq, &lt, &lend, &nt);
             if (code)
                 break;
+            adv_after = lend == nt;  // this claim took the request's last tiles
         }
         const uint32_t slot = tail % kRing;
         ring.d[slot] = ld;
@@ -410,6 +452,19 @@ __device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
         backoff = 32;
         __threadfence_block();
         ring.tail = tail + 1;
+        if (adv_after && lt >= lend) {
+            // All of this request's tiles are claimed and ours are queued:
+            // move the cursor on now instead of waiting for a claim to fail
+            // (without waiting, if the next request is not ready).
+            adv_after = false;
+            if (atomicCAS(p.adv, (unsigned long long)lseq, (unsigned long long)((lseq + 1) & kSeqMask)) == lseq) {
+                const uint32_t r = advance(p, lseq, last_work, stop, false);
+                if (r && r != kNotReady) {
+                    code = r;
+                    break;
+                }
+            }
+        }
     }
     __threadfence_block();
     ring.exit_code = code;
@@ -680,10 +735,10 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     std::memset(s->done, 0, sizeof(unsigned long long) * slots);
     std::memset(s->ctrl, 0, 64);
     // device: cursor, adv and disp each on a 4 KiB page of their own (every
-    // agent polls them), then disp_slot, recs, keys, key_nr
+    // agent polls them), then disp_ring, recs, keys, key_nr
     const size_t off_adv = 4096, off_disp = 8192, off_slots = 12288;
     const size_t off_recs = 16384;
-    static_assert(4 * kDispRing <= 4096, "disp_slot fits in its page");
+    static_assert(8 * kDispRing <= 4096, "disp_ring fits in its page");
     const size_t off_keys = off_recs + sizeof(SrvRec) * (size_t)slots;
     const size_t off_nr = off_keys + 240 * (size_t)max_keys;
     const size_t dbytes = off_nr + sizeof(int) * (size_t)max_keys;
@@ -702,7 +757,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     P.cursor = reinterpret_cast<unsigned long long *>(s->dmem);
     P.adv = reinterpret_cast<unsigned long long *>(s->dmem + off_adv);
     P.disp = reinterpret_cast<unsigned long long *>(s->dmem + off_disp);
-    P.disp_slot = reinterpret_cast<unsigned int *>(s->dmem + off_slots);
+    P.disp_ring = reinterpret_cast<unsigned long long *>(s->dmem + off_slots);
     P.recs = reinterpret_cast<SrvRec *>(s->dmem + off_recs);
     P.keys = reinterpret_cast<const uint4 *>(s->dmem + off_keys);
     P.key_nr = reinterpret_cast<const int *>(s->dmem + off_nr);
