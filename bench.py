@@ -506,6 +506,59 @@ def reroute_sweep(args, rank, local):
     return 0
 
 
+def emulated_study(args, rank, local):
+    """Latency under offered load over a controlled emulated offload (the
+    paper's one emulated experiment: open-loop Poisson arrivals, 20 us
+    offload): per offered rate, p50/p99 latency and achieved rate of a
+    blocking server (each of 8 threads waits for its offload before taking
+    the next request) and of an overlapping one (threads submit at arrival
+    and poll), both through the served path (offload_submit_emulated)."""
+    import torch
+
+    from paper_2607_02630_gb300 import aesoffload as A
+    from paper_2607_02630_gb300 import build as libbuild
+
+    torch.cuda.set_device(local)
+    libbuild.build()
+    A.lib()
+    rates = [float(x) for x in args.emulated_rates.split(",")]
+    srv = A.Server(slots=4096, max_keys=1, idle_timeout_us=2_000_000)
+    rows = []
+    try:
+        warm = np.zeros(2000, dtype=A.drive_dtype())
+        A.drive_served(srv, warm, 8, emulated_ns=args.emulated_ns)
+        for i, rate in enumerate(rates):
+            n = int(min(max(4000, rate * args.emulated_seconds), 400_000))
+            reqs = np.zeros(n, dtype=A.drive_dtype())
+            reqs["arrival_s"] = W.poisson_arrivals(n, rate, seed=W.SEED_BASE + 60 + i)
+            row = {"offered_req_per_s": rate, "requests": n}
+            for mode, blocking in (("blocking", True), ("overlap", False)):
+                lat, res = A.drive_served(srv, reqs, 8, blocking=blocking, emulated_ns=args.emulated_ns)
+                ok = lat[lat >= 0]
+                row[mode] = {"p50_us": _pct(ok, 50), "p99_us": _pct(ok, 99),
+                             "achieved_req_per_s": round(len(ok) / res["elapsed_s"], 1), "errors": res["errors"]}
+            rows.append(row)
+    finally:
+        srv.close()
+
+    def knee(mode):
+        base = rows[0][mode]["p99_us"]
+        best = None
+        for r in rows:
+            m = r[mode]
+            if m["achieved_req_per_s"] >= 0.95 * r["offered_req_per_s"] and m["p99_us"] <= 10 * base:
+                best = r["offered_req_per_s"]
+        return best
+
+    out = {"metric": "latency under offered load over an emulated offload: blocking vs overlapping server",
+           "unit": "us", "offload_ns": args.emulated_ns, "threads": 8, "rows": rows,
+           "knee_req_per_s": {"blocking": knee("blocking"), "overlap": knee("overlap")},
+           "knee_rule": "highest offered rate served at >= 95 % with p99 <= 10x the lowest-rate p99"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------- our arm
 
 def main():
@@ -532,6 +585,12 @@ def main():
     ap.add_argument("--reroute-sizes", default=",".join(str(4096 << k) for k in range(17)))
     ap.add_argument("--reroute-clients", type=int, default=50)
     ap.add_argument("--reroute-seconds", type=float, default=2.0)
+    ap.add_argument("--emulated", action="store_true",
+                    help="open-loop study over an emulated offload: blocking vs overlapping server")
+    ap.add_argument("--emulated-ns", type=int, default=20_000)
+    ap.add_argument("--emulated-rates", default="25000,50000,100000,150000,200000,250000,300000,400000,500000,"
+                                                "600000,800000")
+    ap.add_argument("--emulated-seconds", type=float, default=0.5)
     ap.add_argument("--served", action="store_true",
                     help="served-mode studies: open-loop Poisson rates and the large 8 MiB stream")
     ap.add_argument("--served-requests", type=int, default=20000)
@@ -543,6 +602,8 @@ def main():
         return sweep(args, rank, local)
     if args.reroute:
         return reroute_sweep(args, rank, local)
+    if args.emulated:
+        return emulated_study(args, rank, local)
     if args.served:
         return served(args, rank, local)
 

@@ -261,6 +261,15 @@ int offload_key_register(offload_server_t srv, const uint8_t *key, int bits, int
 int offload_submit(offload_server_t srv, int key_slot, const uint8_t *iv, const void *in,
                    void *out, size_t len, uint64_t *ticket);
 
+/* Emulated offload for controlled-load studies (the paper sweeps offered
+ * load over a fixed 20 us emulated offload, Sec. 6 "Latency under offered
+ * load"): the request takes the whole served path -- queue entry, dispatch,
+ * claim, completion flag -- but its single tile holds one worker warp for
+ * duration_ns instead of encrypting; it moves no data and needs no key.
+ * Poll it like any ticket.  Errors: AES_EINVAL (duration_ns > 10 ms, null
+ * ticket), AES_EAGAIN (no slot free), AES_ESTOPPED, AES_ECUDA. */
+int offload_submit_emulated(offload_server_t srv, uint64_t duration_ns, uint64_t *ticket);
+
 /* AES_OK once the request is complete and its output visible to the host
  * and to later GPU work (the ticket is then released; polling it again gives
  * AES_EINVAL), AES_PENDING while in flight, AES_EDESC if the device rejected
@@ -321,6 +330,21 @@ typedef struct {
  * (back-pressure) is retried.  Errors: AES_EINVAL for bad arguments. */
 int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int nthreads,
                   double *latency_us, aes_drive_result_t *res);
+
+/* Driver options.  blocking != 0: each thread serves its requests one at a
+ * time, waiting for each offload before taking the next (the blocking server
+ * of Sec. 6; latency still counts from the scheduled arrival); 0: threads
+ * submit at arrival and poll all their pending requests (the overlapping,
+ * rerouted server).  emulated_ns > 0: every request is an emulated offload
+ * of that duration (offload_submit_emulated; only arrival_s is read). */
+typedef struct {
+    int blocking;
+    uint64_t emulated_ns;
+} aes_drive_opts_t;
+
+/* offload_drive with options (NULL = offload_drive). */
+int offload_drive_ex(offload_server_t srv, const aes_drive_req_t *reqs, int n, int nthreads,
+                     const aes_drive_opts_t *opts, double *latency_us, aes_drive_result_t *res);
 
 /* Per-call path with the same schedule: each thread owns a CUDA stream,
  * launches aes_ctr, records an event and polls it with cudaEventQuery (the

@@ -74,6 +74,10 @@ class ServerStats(ctypes.Structure):
                 ("kernel_status", ctypes.c_uint32), ("running", ctypes.c_int)]
 
 
+class DriveOpts(ctypes.Structure):
+    _fields_ = [("blocking", ctypes.c_int), ("emulated_ns", ctypes.c_uint64)]
+
+
 class DriveResult(ctypes.Structure):
     _fields_ = [("elapsed_s", ctypes.c_double), ("bytes", ctypes.c_uint64),
                 ("eagain_retries", ctypes.c_uint64), ("errors", ctypes.c_int)]
@@ -115,6 +119,9 @@ _SIGS = {
                                          ctypes.c_uint64]),
     "offload_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "offload_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "offload_submit_emulated": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    "offload_drive_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(DriveOpts), ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
     "offload_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
     "aes_ctr_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -337,6 +344,14 @@ class Server:
         _check(rc, "offload_submit")
         return t
 
+    def submit_emulated(self, duration_ns: int) -> int:
+        """offload_submit_emulated: an emulated offload holding one worker warp
+        for duration_ns; returns its ticket."""
+        t = ctypes.c_uint64(0)
+        _check(lib().offload_submit_emulated(self.handle, int(duration_ns), ctypes.byref(t)),
+               "offload_submit_emulated")
+        return t.value
+
     def poll(self, ticket: int) -> int:
         return lib().offload_poll(self.handle, ctypes.c_uint64(ticket))
 
@@ -388,15 +403,18 @@ def _drive_result(res: DriveResult) -> dict:
             "errors": res.errors}
 
 
-def drive_served(server: "Server", reqs, nthreads: int = 8):
-    """offload_drive over a drive_dtype() array; returns (latency_us array, result dict)."""
+def drive_served(server: "Server", reqs, nthreads: int = 8, blocking: bool = False, emulated_ns: int = 0):
+    """offload_drive_ex over a drive_dtype() array; returns (latency_us array,
+    result dict).  blocking: each thread waits for its offload before the
+    next request; emulated_ns > 0: emulated offloads of that duration."""
     import numpy as np
 
     reqs = np.ascontiguousarray(reqs, dtype=drive_dtype())
     lat = np.zeros(len(reqs), np.float64)
     res = DriveResult()
-    _check(lib().offload_drive(server.handle, reqs.ctypes.data, len(reqs), int(nthreads), lat.ctypes.data,
-                               ctypes.byref(res)), "offload_drive")
+    opts = DriveOpts(1 if blocking else 0, int(emulated_ns))
+    _check(lib().offload_drive_ex(server.handle, reqs.ctypes.data, len(reqs), int(nthreads), ctypes.byref(opts),
+                                  lat.ctypes.data, ctypes.byref(res)), "offload_drive_ex")
     return lat, _drive_result(res)
 
 

@@ -9,7 +9,9 @@
 // scheduled arrival time (never earlier; late if the thread is behind, which
 // counts against the latency, so there is no coordinated omission), and its
 // latency is the time from the scheduled arrival to the moment the thread
-// observes completion.
+// observes completion.  The served driver also runs the paper's blocking
+// server (a thread takes its next request only when the previous offload is
+// done) and the controlled emulated offload of its load study.
 #include "../../include/aesoffload.h"
 #include "internal.h"
 #include "runtime.h"
@@ -53,15 +55,32 @@ using namespace aesrt;
 
 extern "C" {
 
-int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int nthreads,
-                  double *latency_us, aes_drive_result_t *res)
+int offload_drive_ex(offload_server_t srv, const aes_drive_req_t *reqs, int n, int nthreads,
+                     const aes_drive_opts_t *opts, double *latency_us, aes_drive_result_t *res)
 {
     if (!srv || (n > 0 && (!reqs || !latency_us)) || n < 0 || nthreads < 1 || nthreads > 256 || !res)
         return AES_EINVAL;
+    const bool blocking = opts && opts->blocking;
+    const uint64_t emulated_ns = opts ? opts->emulated_ns : 0;
     int dev = 0;
     cudaGetDevice(&dev);
     Shared sh;
     const clk::time_point t0 = clk::now();
+    auto submit = [&](int i, uint64_t *t) {
+        const aes_drive_req_t &r = reqs[i];
+        return emulated_ns ? offload_submit_emulated(srv, emulated_ns, t)
+                           : offload_submit(srv, r.key_slot, r.iv, r.in, r.out, r.len, t);
+    };
+    auto finish = [&](int idx, int rc, double now) {
+        if (rc == AES_OK) {
+            latency_us[idx] = (now - reqs[idx].arrival_s) * 1e6;
+            sh.bytes.fetch_add(emulated_ns ? 0 : reqs[idx].len);
+            note_done(sh, now);
+        } else {
+            latency_us[idx] = -1.0;
+            sh.errors.fetch_add(1);
+        }
+    };
     auto worker = [&](int k) {
         cudaSetDevice(dev);
         std::vector<std::pair<uint64_t, int>> pending;  // (ticket, request index)
@@ -77,10 +96,10 @@ int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int 
                 sh.errors.fetch_add((int)pending.size());
                 break;
             }
-            if (next < n && seconds_since(t0) >= reqs[next].arrival_s) {
-                const aes_drive_req_t &r = reqs[next];
+            // blocking: a request is taken only once the previous one is done
+            if (next < n && (!blocking || pending.empty()) && seconds_since(t0) >= reqs[next].arrival_s) {
                 uint64_t t = 0;
-                const int rc = offload_submit(srv, r.key_slot, r.iv, r.in, r.out, r.len, &t);
+                const int rc = submit(next, &t);
                 if (rc == AES_OK) {
                     pending.emplace_back(t, next);
                     next += nthreads;
@@ -88,8 +107,7 @@ int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int 
                 } else if (rc == AES_EAGAIN) {
                     sh.retries.fetch_add(1);  // back-pressure: poll below, then retry
                 } else {
-                    latency_us[next] = -1.0;
-                    sh.errors.fetch_add(1);
+                    finish(next, rc, 0.0);
                     next += nthreads;
                 }
             }
@@ -99,17 +117,9 @@ int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int 
                     ++i;
                     continue;
                 }
-                const int idx = pending[i].second;
                 const double now = seconds_since(t0);
                 last_progress = now;
-                if (rc == AES_OK) {
-                    latency_us[idx] = (now - reqs[idx].arrival_s) * 1e6;
-                    sh.bytes.fetch_add(reqs[idx].len);
-                    note_done(sh, now);
-                } else {
-                    latency_us[idx] = -1.0;
-                    sh.errors.fetch_add(1);
-                }
+                finish(pending[i].second, rc, now);
                 pending[i] = pending.back();
                 pending.pop_back();
             }
@@ -126,6 +136,12 @@ int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int 
     res->eagain_retries = sh.retries.load();
     res->errors = sh.errors.load();
     return sh.timed_out.load() ? AES_ETIMEOUT : AES_OK;
+}
+
+int offload_drive(offload_server_t srv, const aes_drive_req_t *reqs, int n, int nthreads,
+                  double *latency_us, aes_drive_result_t *res)
+{
+    return offload_drive_ex(srv, reqs, n, nthreads, nullptr, latency_us, res);
 }
 
 int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, int n, int nthreads,

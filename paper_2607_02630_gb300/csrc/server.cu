@@ -69,6 +69,9 @@ constexpr uint32_t kMaxTiles = (1u << kTileBits) - 16384;  // headroom for batch
 constexpr int kMaxSlots = 65535;
 constexpr uint32_t kExitStop = 1, kExitIdle = 2, kExitError = 4;
 constexpr uint32_t kNotReady = 8;  // advance(): next request not ready (not an exit reason)
+constexpr uint32_t kFlagHostOut = 1;   // QEntry.flags: the output is pinned host memory
+constexpr uint32_t kFlagEmulated = 2;  // QEntry.flags: emulated offload, len = duration in ns
+constexpr uint64_t kMaxEmulatedNs = 10000000;
 constexpr int kMaxWarps = 24;   // CTA of at most 768 threads (80 registers each)
 constexpr uint32_t kRing = 64;  // >= workers + prefetch
 // Tiles an agent keeps queued for its workers.  A deep queue rides through
@@ -85,7 +88,7 @@ struct QEntry {  // 64 bytes, host-written, tag last
     uint64_t in, out, len, iv_hi, iv_lo, gen;
     uint32_t key_slot;
     uint16_t desc;   // slot index d
-    uint16_t flags;  // bit 0: the output is pinned host memory
+    uint16_t flags;  // kFlagHostOut, kFlagEmulated
 };
 static_assert(sizeof(QEntry) == 64, "QEntry layout");
 
@@ -240,7 +243,12 @@ __device__ __noinline__ uint32_t dispatch(const SrvParams &p, uint32_t k0, uint3
         if (ok && len)
             ok = in && out && !((in | out) & 15u);
         uint32_t ntiles = 0, tg = 1, tp = 1;
-        if (ok && len) {
+        const bool emulated = (flags & kFlagEmulated) != 0;
+        if (emulated) {  // one tile that holds a worker warp for len ns; no key, no payload
+            ok = len <= kMaxEmulatedNs;
+            ntiles = ok ? 1u : 0u;
+            nr = 0;
+        } else if (ok && len) {
             // tiles are runs of tg whole 256-block counter groups, or (tp > 1)
             // equal parts of one group.  Unless fixed by the server config, a
             // request is cut into about 512 tiles of 64..1024 blocks: short
@@ -265,7 +273,7 @@ __device__ __noinline__ uint32_t dispatch(const SrvParams &p, uint32_t k0, uint3
         rec->rq.len = len;
         rec->rq.iv_hi = iv_hi;
         rec->rq.iv_lo = iv_lo;
-        rec->rq.rk = p.keys + 15u * (ok ? ks : 0u);
+        rec->rq.rk = p.keys + 15u * (ok && !emulated ? ks : 0u);
         rec->rq.nr = (uint32_t)nr;
         rec->rq.pad = flags;
         rec->gen = x[i][5];
@@ -543,18 +551,28 @@ __global__ void __launch_bounds__(768, 1) server_kernel(const __grid_constant__ 
             cur_d = d;
             cur_seq = seq;
         }
-        uint64_t first, last;
-        const uint32_t part = t % tp;
-        aestile::tile_blocks_of(t / tp, tg, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
-        switch (rq.nr) {
-        case 10: aestile::run_tile_warp<10, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
-        case 12: aestile::run_tile_warp<12, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
-        default: aestile::run_tile_warp<14, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
+        if (rq.pad & kFlagEmulated) {
+            // emulated offload: hold this warp for rq.len ns (at most kMaxEmulatedNs)
+            if (lane == 0) {
+                const uint64_t t_end = gtime() + rq.len;
+                while (gtime() < t_end)
+                    __nanosleep(256);
+            }
+            __syncwarp();
+        } else {
+            uint64_t first, last;
+            const uint32_t part = t % tp;
+            aestile::tile_blocks_of(t / tp, tg, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
+            switch (rq.nr) {
+            case 10: aestile::run_tile_warp<10, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
+            case 12: aestile::run_tile_warp<12, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
+            default: aestile::run_tile_warp<14, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
+            }
         }
         // Order this lane's output stores before the tile is counted: at
         // system scope when the output lives in host memory, else GPU scope
         // (the completing thread's system-scope release covers the rest).
-        if (rq.pad & 1u)
+        if (rq.pad & kFlagHostOut)
             __threadfence_system();
         else
             __threadfence();
@@ -652,6 +670,59 @@ void release_slot(offload_server_s *s, uint32_t d)
     s->inflight.fetch_sub(s->bytes[d]);
     std::lock_guard<std::mutex> lk(s->mu);
     s->free_slots.push_back(d);
+}
+
+// Admission (HBM budget, then a free slot) and the queue entry of one
+// request; the tag is stored last with release semantics.
+int enqueue(offload_server_s *s, uint32_t key_slot, uint64_t iv_hi, uint64_t iv_lo, const void *din, void *dout,
+            uint64_t len, uint32_t flags, uint64_t charge, uint64_t *ticket)
+{
+    if (s->budget) {
+        uint64_t cur = s->inflight.load();
+        do {
+            if (cur + charge > s->budget) {
+                s->n_again.fetch_add(1);
+                return AES_EAGAIN;
+            }
+        } while (!s->inflight.compare_exchange_weak(cur, cur + charge));
+    } else {
+        s->inflight.fetch_add(charge);
+    }
+    uint32_t d;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->free_slots.empty()) {
+            s->inflight.fetch_sub(charge);
+            s->n_again.fetch_add(1);
+            return AES_EAGAIN;
+        }
+        d = s->free_slots.back();
+        s->free_slots.pop_back();
+    }
+    const uint64_t gen = ++s->gen[d];
+    s->bytes[d] = charge;
+    s->lens[d] = flags & kFlagEmulated ? 0 : len;
+    const uint64_t tk = (gen << 16) | d;
+    s->live[d].store(tk);
+    // A slot is admitted only while fewer than `slots` requests are in
+    // flight and the device reads entries in sequence order, so the entry of
+    // seq - qsize (qsize >= slots) has been read before this one reuses it.
+    const uint64_t seq = s->next_seq.fetch_add(1);
+    QEntry &qe = s->queue[seq & (s->qsize - 1)];
+    qe.in = (uint64_t)(uintptr_t)din;
+    qe.out = (uint64_t)(uintptr_t)dout;
+    qe.len = len;
+    qe.iv_hi = iv_hi;
+    qe.iv_lo = iv_lo;
+    qe.gen = gen;
+    qe.key_slot = key_slot;
+    qe.desc = (uint16_t)d;
+    qe.flags = (uint16_t)flags;
+    __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
+    s->n_sub.fetch_add(1);
+    *ticket = tk;
+    const int rc = ensure_running(s);
+    return rc == AES_ESTOPPED ? AES_OK : rc;
 }
 
 }  // namespace
@@ -858,52 +929,19 @@ int offload_submit(offload_server_t s, int key_slot, const uint8_t *iv, const vo
     const uint64_t charge = len == 0 ? 0 : (in == out ? (uint64_t)len : 2ull * len);
     if (s->budget && charge > s->budget)
         return AES_ETOOBIG;
-    // admission: budget, then a free slot
-    if (s->budget) {
-        uint64_t cur = s->inflight.load();
-        do {
-            if (cur + charge > s->budget) {
-                s->n_again.fetch_add(1);
-                return AES_EAGAIN;
-            }
-        } while (!s->inflight.compare_exchange_weak(cur, cur + charge));
-    } else {
-        s->inflight.fetch_add(charge);
-    }
-    uint32_t d;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        if (s->free_slots.empty()) {
-            s->inflight.fetch_sub(charge);
-            s->n_again.fetch_add(1);
-            return AES_EAGAIN;
-        }
-        d = s->free_slots.back();
-        s->free_slots.pop_back();
-    }
-    const uint64_t gen = ++s->gen[d];
-    s->bytes[d] = charge;
-    s->lens[d] = len;
-    const uint64_t tk = (gen << 16) | d;
-    s->live[d].store(tk);
-    // A slot is admitted only while fewer than `slots` requests are in
-    // flight and the device reads entries in sequence order, so the entry of
-    // seq - qsize (qsize >= slots) has been read before this one reuses it.
-    const uint64_t seq = s->next_seq.fetch_add(1);
-    QEntry &qe = s->queue[seq & (s->qsize - 1)];
-    qe.in = (uint64_t)(uintptr_t)din;
-    qe.out = (uint64_t)(uintptr_t)dout;
-    qe.len = len;
-    iv_halves(iv, &qe.iv_hi, &qe.iv_lo);
-    qe.gen = gen;
-    qe.key_slot = (uint32_t)key_slot;
-    qe.desc = (uint16_t)d;
-    qe.flags = out_host ? 1u : 0u;
-    __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
-    s->n_sub.fetch_add(1);
-    *ticket = tk;
-    const int rc = ensure_running(s);
-    return rc == AES_ESTOPPED ? AES_OK : rc;
+    uint64_t iv_hi = 0, iv_lo = 0;
+    iv_halves(iv, &iv_hi, &iv_lo);
+    return enqueue(s, (uint32_t)key_slot, iv_hi, iv_lo, din, dout, len, out_host ? kFlagHostOut : 0u, charge,
+                   ticket);
+}
+
+int offload_submit_emulated(offload_server_t s, uint64_t duration_ns, uint64_t *ticket)
+{
+    if (!s || !ticket || duration_ns > kMaxEmulatedNs)
+        return AES_EINVAL;
+    if (s->stopping.load())
+        return AES_ESTOPPED;
+    return enqueue(s, 0, 0, 0, nullptr, nullptr, duration_ns, kFlagEmulated, 0, ticket);
 }
 
 int offload_poll(offload_server_t s, uint64_t ticket)

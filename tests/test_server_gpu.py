@@ -6,6 +6,7 @@ tickets, idle exit + relaunch and the stop path.  Every device wait in the
 resident kernel is bounded, so none of these can hang the GPU; host waits
 use offload_wait with a timeout.
 """
+import ctypes
 import threading
 import time
 
@@ -386,5 +387,42 @@ def test_poll_many(cuda, aes, ncpu):
         for i, n in enumerate(sizes):
             o = int(offs[i])
             np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, 128, ivs[i], payload[o: o + n], ncpu))
+    finally:
+        assert srv.close() == aes.AES_OK
+
+
+def test_emulated_offload(cuda, aes):
+    """An emulated offload takes the whole served path but holds a worker warp
+    for its duration instead of encrypting; it moves no bytes."""
+    srv = aes.Server(slots=16, max_keys=1, ctas=8, idle_timeout_us=500_000)
+    try:
+        t0 = time.perf_counter()
+        t = srv.submit_emulated(2_000_000)
+        assert srv.wait(t, WAIT_US) == aes.AES_OK
+        assert time.perf_counter() - t0 >= 0.002
+        tickets = [srv.submit_emulated(20_000) for _ in range(12)]
+        for t in tickets:
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+        st = srv.stats()
+        assert st["completed"] == 13 and st["bytes_completed"] == 0
+        tk = ctypes.c_uint64(0)
+        assert aes.lib().offload_submit_emulated(srv.handle, 20_000_000, ctypes.byref(tk)) == aes.AES_EINVAL
+    finally:
+        assert srv.close() == aes.AES_OK
+
+
+@pytest.mark.parametrize("blocking", [True, False])
+def test_emulated_open_loop_drivers(cuda, aes, blocking):
+    """The blocking and overlapping servers of the load study, over emulated
+    20 us offloads: every request completes, none faster than its offload."""
+    srv = aes.Server(slots=64, max_keys=1, ctas=16, idle_timeout_us=500_000)
+    try:
+        n = 600
+        reqs = np.zeros(n, dtype=aes.drive_dtype())
+        reqs["arrival_s"] = W.poisson_arrivals(n, 30_000.0, seed=69)
+        lat, res = aes.drive_served(srv, reqs, 4, blocking=blocking, emulated_ns=20_000)
+        assert res["errors"] == 0
+        assert (lat >= 20.0).all()
+        assert res["bytes"] == 0
     finally:
         assert srv.close() == aes.AES_OK
