@@ -353,6 +353,53 @@ int offload_drive_ex(offload_server_t srv, const aes_drive_req_t *reqs, int n, i
 int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, int n, int nthreads,
                   double *latency_us, aes_drive_result_t *res);
 
+/* ------------------------------------------------ shared-state conflicts */
+
+/* The page-protection conflict detector (Sec. 5, "A transparent conflict
+ * detector") measured on a synthetic server: `handlers` cooperative handlers
+ * on the calling thread serve `requests` requests; each reads one of
+ * `counters` shared counters (`counters_per_page` to a page, 1..64), parks
+ * at an offload, and writes the counter back incremented -- the unlocked
+ * read-modify-write that rerouting exposes.  The detector write-protects the
+ * counters' pages, snapshots a version clock when a handler parks, and flags
+ * a write fault on a page modified during the park; CDET_ENFORCE restarts a
+ * conflicting handler and re-runs it serialized.  The offload: a host timer
+ * of offload_ns when srv is NULL; else the served path -- an emulated
+ * offload of offload_ns when bytes == 0, or AES-CTR of `bytes` with key
+ * `key_slot` from buf_in + h*stride to buf_out + h*stride for handler h
+ * (stride = bytes rounded up to 256).  Installs a SIGSEGV handler for the
+ * duration (the previous one is restored; faults outside the detector's
+ * pages go to it); one run at a time per process.  Synchronous.  Errors:
+ * AES_EINVAL, AES_ENOMEM, or the offload's error. */
+#define CDET_UNPROTECTED 0 /* overlap, nothing guards the counters */
+#define CDET_LOCK 1        /* one coarse lock held across the offload */
+#define CDET_DETECT 2      /* overlap, conflicts counted, not prevented */
+#define CDET_ENFORCE 3     /* overlap, conflicting handlers re-run serialized */
+
+typedef struct {
+    int handlers;
+    int requests;
+    int counters;
+    int counters_per_page;
+    int mode;
+    uint64_t offload_ns;
+    offload_server_t srv;
+    int key_slot;
+    const void *buf_in;
+    void *buf_out;
+    size_t bytes;
+} cdet_run_cfg_t;
+
+typedef struct {
+    uint64_t final_count;   /* sum of the counters (requests if no update was lost) */
+    uint64_t lost_updates;  /* requests - final_count */
+    uint64_t conflicts;     /* write faults on a page modified during the writer's park */
+    uint64_t restarts;      /* handlers re-run serialized (CDET_ENFORCE) */
+    double elapsed_s;
+} cdet_run_result_t;
+
+int cdet_run(const cdet_run_cfg_t *cfg, cdet_run_result_t *res);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,21 @@ class ServerStats(ctypes.Structure):
                 ("kernel_status", ctypes.c_uint32), ("running", ctypes.c_int)]
 
 
+class CdetCfg(ctypes.Structure):
+    _fields_ = [("handlers", ctypes.c_int), ("requests", ctypes.c_int), ("counters", ctypes.c_int),
+                ("counters_per_page", ctypes.c_int), ("mode", ctypes.c_int), ("offload_ns", ctypes.c_uint64),
+                ("srv", ctypes.c_void_p), ("key_slot", ctypes.c_int), ("buf_in", ctypes.c_void_p),
+                ("buf_out", ctypes.c_void_p), ("bytes", ctypes.c_size_t)]
+
+
+class CdetResult(ctypes.Structure):
+    _fields_ = [("final_count", ctypes.c_uint64), ("lost_updates", ctypes.c_uint64), ("conflicts", ctypes.c_uint64),
+                ("restarts", ctypes.c_uint64), ("elapsed_s", ctypes.c_double)]
+
+
+CDET_UNPROTECTED, CDET_LOCK, CDET_DETECT, CDET_ENFORCE = 0, 1, 2, 3
+
+
 class DriveOpts(ctypes.Structure):
     _fields_ = [("blocking", ctypes.c_int), ("emulated_ns", ctypes.c_uint64)]
 
@@ -122,6 +137,7 @@ _SIGS = {
     "offload_submit_emulated": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     "offload_drive_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(DriveOpts), ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
+    "cdet_run": (ctypes.c_int, [ctypes.POINTER(CdetCfg), ctypes.POINTER(CdetResult)]),
     "offload_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
     "aes_ctr_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -429,3 +445,19 @@ def drive_per_call(ctxs, reqs, nthreads: int = 8):
     _check(lib().aes_ctr_drive(handles, len(ctxs), reqs.ctypes.data, len(reqs), int(nthreads),
                                lat.ctypes.data, ctypes.byref(res)), "aes_ctr_drive")
     return lat, _drive_result(res)
+
+
+def conflict_run(mode: int, handlers: int = 16, requests: int = 4000, counters: int = 64, counters_per_page: int = 1,
+                 offload_ns: int = 50_000, server: "Server | None" = None, key_slot: int = 0, buf_in=0, buf_out=0,
+                 nbytes: int = 0) -> dict:
+    """cdet_run: the conflict detector's synthetic server (read a shared
+    counter, park at an offload, write it back incremented) in one of the
+    CDET_* modes; returns the result as a dict (requests/s added)."""
+    cfg = CdetCfg(int(handlers), int(requests), int(counters), int(counters_per_page), int(mode), int(offload_ns),
+                  server.handle if server else None, int(key_slot), ptr(buf_in) if buf_in else None,
+                  ptr(buf_out) if buf_out else None, int(nbytes))
+    res = CdetResult()
+    _check(lib().cdet_run(ctypes.byref(cfg), ctypes.byref(res)), "cdet_run")
+    out = {f: getattr(res, f) for f, _ in CdetResult._fields_}
+    out["req_per_s"] = requests / res.elapsed_s if res.elapsed_s > 0 else 0.0
+    return out

@@ -1,0 +1,71 @@
+"""The page-protection conflict detector on its synthetic server (handlers
+read a shared counter, park at an offload, write it back incremented), with a
+host-timed offload, on the CPU (Sec. 5: unlocked shared aggregates lose
+updates under overlap; the detector flags the conflicts and, enforcing,
+re-runs conflicting handlers serialized)."""
+import pytest
+
+from paper_2607_02630_gb300 import aesoffload as A
+
+N = 3000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2607_02630_gb300 import build
+
+    build.build()
+
+
+def run(mode, counters=64, handlers=16, offload_ns=50_000, requests=N):
+    return A.conflict_run(mode, handlers=handlers, requests=requests, counters=counters, offload_ns=offload_ns)
+
+
+def test_unprotected_overlap_loses_updates():
+    r = run(A.CDET_UNPROTECTED, counters=1)
+    assert r["lost_updates"] > N // 2
+    assert r["final_count"] + r["lost_updates"] == N
+    assert r["conflicts"] == 0
+
+
+def test_coarse_lock_loses_nothing():
+    r = run(A.CDET_LOCK)
+    assert r["lost_updates"] == 0 and r["final_count"] == N
+
+
+def test_detect_flags_every_lost_update():
+    r = run(A.CDET_DETECT)
+    assert r["lost_updates"] > 0
+    assert r["conflicts"] >= r["lost_updates"]
+    assert r["restarts"] == 0
+
+
+def test_enforce_loses_nothing_and_beats_the_lock():
+    enf = run(A.CDET_ENFORCE)
+    lock = run(A.CDET_LOCK)
+    assert enf["lost_updates"] == 0 and enf["final_count"] == N
+    assert enf["conflicts"] > 0 and enf["restarts"] == enf["conflicts"]
+    assert enf["req_per_s"] > 1.5 * lock["req_per_s"]
+
+
+def test_single_handler_never_conflicts():
+    r = run(A.CDET_ENFORCE, counters=1, handlers=1, requests=300, offload_ns=10_000)
+    assert r["lost_updates"] == 0 and r["conflicts"] == 0
+
+
+def test_false_sharing_is_conservative():
+    """Counters sharing a page conflict at page granularity: more conflicts
+    than with one counter per page, still no lost update when enforcing."""
+    per_page = A.conflict_run(A.CDET_ENFORCE, handlers=16, requests=N, counters=64, counters_per_page=64)
+    own_page = run(A.CDET_ENFORCE)
+    assert per_page["lost_updates"] == 0
+    assert per_page["conflicts"] > own_page["conflicts"]
+
+
+def test_bad_arguments():
+    with pytest.raises(A.AesError):
+        A.conflict_run(A.CDET_LOCK, handlers=0)
+    with pytest.raises(A.AesError):
+        A.conflict_run(7)
+    with pytest.raises(A.AesError):
+        A.conflict_run(A.CDET_LOCK, counters_per_page=65)
