@@ -454,8 +454,8 @@ def conflict_run(mode: int, handlers: int = 16, requests: int = 4000, counters: 
     counter, park at an offload, write it back incremented) in one of the
     CDET_* modes; returns the result as a dict (requests/s added)."""
     cfg = CdetCfg(int(handlers), int(requests), int(counters), int(counters_per_page), int(mode), int(offload_ns),
-                  server.handle if server else None, int(key_slot), ptr(buf_in) if buf_in else None,
-                  ptr(buf_out) if buf_out else None, int(nbytes))
+                  server.handle if server else None, int(key_slot), ptr(buf_in) or None, ptr(buf_out) or None,
+                  int(nbytes))
     res = CdetResult()
     _check(lib().cdet_run(ctypes.byref(cfg), ctypes.byref(res)), "cdet_run")
     out = {f: getattr(res, f) for f, _ in CdetResult._fields_}
