@@ -561,10 +561,12 @@ def emulated_study(args, rank, local):
 
 def conflict_study(args, rank, local):
     """The conflict detector with a real GPU offload: 16 handlers on one
-    event loop serve requests that read one of 64 shared counters, park at a
-    1 MiB AES-128-CTR served request, and write the counter back incremented;
-    lost updates, conflicts and requests/s for unprotected overlap, a coarse
-    lock, detection only, and enforcement."""
+    event loop serve requests that read one of 64 shared counters, park at an
+    AES-128-CTR served request (1 MiB and 8 MiB), and write the counter back
+    incremented; lost updates, conflicts and requests/s for unprotected
+    overlap, a coarse lock, detection only, and enforcement.  Also the cost
+    of one guarded write in this (CUDA) process: one handler, no offload,
+    detection on vs off."""
     import torch
 
     from paper_2607_02630_gb300 import aesoffload as A
@@ -574,30 +576,44 @@ def conflict_study(args, rank, local):
     libbuild.build()
     A.lib()
     dev = torch.device("cuda", local)
-    handlers, nbytes, requests = 16, args.conflict_bytes, args.conflict_requests
-    stride = (nbytes + 255) // 256 * 256
+    handlers, requests = 16, args.conflict_requests
+    sizes = [int(x) for x in args.conflict_bytes.split(",")]
+    stride = (max(sizes) + 255) // 256 * 256
     gen = torch.Generator(device=dev).manual_seed(W.SEED_BASE + 11)
     src = torch.randint(0, 256, (handlers * stride,), dtype=torch.uint8, device=dev, generator=gen)
     dst = torch.empty_like(src)
     srv = A.Server(slots=256, max_keys=1, idle_timeout_us=2_000_000)
-    rows = {}
+    names = {A.CDET_UNPROTECTED: "unprotected", A.CDET_LOCK: "coarse_lock", A.CDET_DETECT: "detect",
+             A.CDET_ENFORCE: "enforce"}
+    studies = []
     try:
         ks = srv.key_register(bytes(W.random_bytes(W.rng(W.SEED_BASE + 12), 16)), 128)
-        names = {A.CDET_UNPROTECTED: "unprotected", A.CDET_LOCK: "coarse_lock", A.CDET_DETECT: "detect",
-                 A.CDET_ENFORCE: "enforce"}
-        A.conflict_run(A.CDET_UNPROTECTED, handlers, 500, 64, server=srv, key_slot=ks, buf_in=src, buf_out=dst,
-                       nbytes=nbytes)  # warm-up
-        for mode, name in names.items():
-            r = A.conflict_run(mode, handlers, requests, 64, server=srv, key_slot=ks, buf_in=src, buf_out=dst,
-                               nbytes=nbytes)
-            rows[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+        for nbytes in sizes:
+            # per-handler buffers at `stride` apart: pass views so the stride matches
+            def run(mode, n):
+                return A.conflict_run(mode, handlers, n, 64, server=srv, key_slot=ks, buf_in=src, buf_out=dst,
+                                      nbytes=nbytes)
+            run(A.CDET_UNPROTECTED, 500)  # warm-up
+            rows = {}
+            for mode, name in names.items():
+                r = run(mode, requests)
+                rows[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+            studies.append({"offload": f"served AES-128-CTR, {nbytes} bytes per request, payload in HBM",
+                            "rows": rows,
+                            "enforce_vs_lock": round(rows["enforce"]["req_per_s"] / rows["coarse_lock"]["req_per_s"], 2),
+                            "enforce_vs_unprotected": round(rows["enforce"]["req_per_s"]
+                                                            / rows["unprotected"]["req_per_s"], 3)})
+        n1 = 5000
+        off = A.conflict_run(A.CDET_UNPROTECTED, 1, n1, 1, offload_ns=0)
+        on = A.conflict_run(A.CDET_DETECT, 1, n1, 1, offload_ns=0)
+        fault_us = (on["elapsed_s"] - off["elapsed_s"]) / n1 * 1e6
     finally:
         srv.close()
     out = {"metric": "shared-counter read-modify-write across a GPU offload: lost updates and req/s by guard",
-           "unit": "req/s", "handlers": handlers, "counters": 64, "requests": requests,
-           "offload": f"served AES-128-CTR, {nbytes} bytes per request, payload in HBM", "rows": rows,
-           "enforce_vs_lock": round(rows["enforce"]["req_per_s"] / rows["coarse_lock"]["req_per_s"], 2),
-           "enforce_vs_unprotected": round(rows["enforce"]["req_per_s"] / rows["unprotected"]["req_per_s"], 3)}
+           "unit": "req/s", "handlers": handlers, "counters": 64, "requests": requests, "studies": studies,
+           "guarded_write_cost_us": round(fault_us, 2),
+           "guarded_write_cost_how": "1 handler, no offload: (detect - unprotected) time per request = one write "
+                                     "fault + two mprotect calls, in this CUDA process"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
@@ -637,7 +653,7 @@ def main():
     ap.add_argument("--emulated-seconds", type=float, default=0.5)
     ap.add_argument("--conflict", action="store_true",
                     help="conflict-detector study (shared counters across a GPU offload)")
-    ap.add_argument("--conflict-bytes", type=int, default=1 << 20)
+    ap.add_argument("--conflict-bytes", default=f"{1 << 20},{8 << 20}")
     ap.add_argument("--conflict-requests", type=int, default=10000)
     ap.add_argument("--served", action="store_true",
                     help="served-mode studies: open-loop Poisson rates and the large 8 MiB stream")
