@@ -398,8 +398,20 @@ def served(args, rank, local):
                          "p50_1mib_us": _pct(lat_pc[one_mib], 50), "p99_1mib_us": _pct(lat_pc[one_mib], 99),
                          "gbs": round(res_pc["bytes"] / res_pc["elapsed_s"] / 1e9, 2), "errors": res_pc["errors"]}})
     srv.close()
+    # the same requests on a server cut for throughput (fixed 1024-block tiles)
+    srv = A.Server(slots=1024, max_keys=64, idle_timeout_us=2_000_000, tile_blocks=1024)
+    slots_t = [srv.key_register(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)]
+    tput_reqs = served_reqs.copy()
+    tput_reqs["key_slot"] = np.array(slots_t)[key_idx]
+    tput_reqs["arrival_s"] = 0.0
+    A.drive_served(srv, tput_reqs, 8)
+    lat_t, res_t = A.drive_served(srv, tput_reqs, 8)
+    srv.close()
+    sat_t = {"req_per_s": round(n / res_t["elapsed_s"], 1), "gbs": round(total / res_t["elapsed_s"] / 1e9, 2),
+             "errors": res_t["errors"], "config": "tile_blocks=1024"}
     out["open_loop"] = {"requests_per_rate": n, "payload_bytes_per_rate": total, "submitter_threads": 8,
-                        "saturation_served": sat, "saturation_per_call": sat_pc, "rates": rates}
+                        "saturation_served": sat, "saturation_served_tile1024": sat_t,
+                        "saturation_per_call": sat_pc, "rates": rates}
     del pool, ring, ctxs
     torch.cuda.empty_cache()
 
