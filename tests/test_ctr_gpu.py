@@ -4,6 +4,7 @@ AES-CTR is deterministic: exactly one output is correct, so every comparison
 here is byte-for-byte (tolerance 0).  Inputs come from the seeded generators
 in paper_2607_02630_gb300.workloads; expected values only from oracle/.
 """
+import re
 import zlib
 
 import numpy as np
@@ -198,6 +199,27 @@ def test_autotune_then_auto_shapes_stay_exact(cuda, aes, ncpu, tmp_path):
         data = W.random_bytes(g, n)
         np.testing.assert_array_equal(gpu_ctr(cuda, aes, ctx, iv, data),
                                       oracle.ctr_mt(key, 256, iv, data, ncpu))
+    # the batch shape was tuned too, and the tuned default stays exact
+    text = open(path).read()
+    m = re.search(r'"batch": \[(\d+), (\d+), (\d+)\]', text)
+    assert m and int(m.group(1)) == 1 and int(m.group(2)) in (256, 384, 512, 1024)
+    assert int(m.group(3)) in (1024, 2048, 4096)
+    lengths = [1, 4096 + 7, 1 << 20, (3 << 20) + 5]
+    total = sum((n + 255) // 256 * 256 for n in lengths)
+    payload = W.random_bytes(g, total)
+    src, dst = to_dev(cuda, payload), to_dev(cuda, np.zeros(0, np.uint8), pad=total)
+    reqs, meta, o = [], [], 0
+    for i, n in enumerate(lengths):
+        bits = (128, 256)[i % 2]
+        key = W.random_bytes(g, bits // 8)
+        iv = W.random_bytes(g, 16)
+        reqs.append((aes.Context(key.tobytes(), bits), iv.tobytes(), src.data_ptr() + o, dst.data_ptr() + o, n))
+        meta.append((key, bits, iv, o, n))
+        o += (n + 255) // 256 * 256
+    aes.batch(reqs)
+    out = to_host(dst)
+    for key, bits, iv, o, n in meta:
+        np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, bits, iv, payload[o: o + n], ncpu))
 
 
 def test_ctr_sync_blocks_until_done(cuda, aes, ncpu):
