@@ -16,7 +16,7 @@ import pytest
 import oracle
 from paper_2607_02630_gb300 import workloads as W
 
-from gpu_util import to_dev, to_host
+from gpu_util import iv_plus, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -426,3 +426,47 @@ def test_emulated_open_loop_drivers(cuda, aes, blocking):
         assert res["bytes"] == 0
     finally:
         assert srv.close() == aes.AES_OK
+
+
+@pytest.mark.parametrize("budget_gib", [20, 2])
+def test_full_size_8mib_aes256_stream_sampled(cuda, aes, ncpu, budget_gib):
+    """The 8 MiB AES-256 stream at full size, as the served study runs it:
+    2048 requests (16 GiB), at most 512 in flight, an HBM budget of 20 GiB
+    and of 2 GiB (back-pressure), a new key every 1024 requests, all offered
+    at once through the native driver.  Sampled against the oracle: every
+    64th request in full and four 4 KiB windows of every request (a window
+    starts at T_1 + offset/16)."""
+    MiB = 1 << 20
+    n5, big = 2048, 8 * MiB
+    gen = cuda.Generator(device="cuda").manual_seed(W.SEED_BASE + 5)
+    src = cuda.randint(0, 256, (n5 * big,), dtype=cuda.uint8, device="cuda", generator=gen)
+    dst = cuda.full((n5 * big,), 0xA5, dtype=cuda.uint8, device="cuda")
+    g = W.rng(W.SEED_BASE + 7)
+    keys5 = [W.random_bytes(g, 32) for _ in range(n5 // 1024)]
+    ivs5 = W.random_bytes(g, 16 * n5).reshape(n5, 16)
+    srv = aes.Server(slots=512, max_keys=4, hbm_budget=budget_gib << 30, idle_timeout_us=2_000_000)
+    try:
+        ks = [srv.key_register(k.tobytes(), 256) for k in keys5]
+        r5 = np.zeros(n5, dtype=aes.drive_dtype())
+        r5["key_slot"] = np.array(ks)[np.arange(n5) // 1024]
+        r5["iv"] = ivs5
+        r5["inp"] = src.data_ptr() + np.arange(n5) * big
+        r5["out"] = dst.data_ptr() + np.arange(n5) * big
+        r5["len"] = big
+        lat, res = aes.drive_served(srv, r5, 8)
+        assert res["errors"] == 0 and (lat > 0).all()
+    finally:
+        assert srv.close() == aes.AES_OK
+    cuda.cuda.synchronize()
+    gw = W.rng(W.SEED_BASE + 8)
+    for i in range(n5):
+        key = keys5[i // 1024]
+        base = i * big
+        spans = [(0, big)] if i % 64 == 0 else []
+        spans += [(int(o) * 16, int(o) * 16 + 4096) for o in gw.integers(0, (big - 4096) // 16, 4)]
+        for a, b in spans:
+            want = oracle.ctr_mt(key, 256, iv_plus(ivs5[i], a // 16), src[base + a: base + b].cpu().numpy(), ncpu)
+            np.testing.assert_array_equal(dst[base + a: base + b].cpu().numpy(), want,
+                                          err_msg=f"request {i} bytes [{a}, {b})")
+    del src, dst
+    cuda.cuda.empty_cache()
