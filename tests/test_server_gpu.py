@@ -470,3 +470,30 @@ def test_full_size_8mib_aes256_stream_sampled(cuda, aes, ncpu, budget_gib):
                                           err_msg=f"request {i} bytes [{a}, {b})")
     del src, dst
     cuda.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("cfg", [dict(threads=64, ctas=2, tile_blocks=64), dict(threads=96, ctas=1, tile_blocks=128),
+                                 dict(threads=512, tile_blocks=256), dict()])
+def test_server_shapes_match_oracle(cuda, aes, ncpu, cfg):
+    """The smallest CTAs (one worker warp), a single CTA, fixed tile sizes and
+    the defaults all give the oracle's bytes on a mix of lengths and keys."""
+    srv = aes.Server(slots=32, max_keys=4, idle_timeout_us=500_000, **cfg)
+    try:
+        g = W.rng(73)
+        keys = [(W.random_bytes(g, b // 8), b) for b in (128, 256, 192)]
+        slots = [srv.key_register(k.tobytes(), b) for k, b in keys]
+        sizes = [0, 15, 16, 17, 4096 + 3, 65536, (1 << 20) + 9]
+        payload, offs, src, dst = arena(cuda, g, sizes)
+        ivs = [W.random_bytes(g, 16) for _ in sizes]
+        tickets = [srv.submit(slots[i % 3], ivs[i].tobytes(), src.data_ptr() + int(offs[i]),
+                              dst.data_ptr() + int(offs[i]), n) for i, n in enumerate(sizes)]
+        for t in tickets:
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+        out = to_host(dst)
+        for i, n in enumerate(sizes):
+            o = int(offs[i])
+            key, bits = keys[i % 3]
+            np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, bits, ivs[i], payload[o: o + n], ncpu))
+            assert (out[o + n: o + n + 16] == 0xA5).all()
+    finally:
+        assert srv.close() == aes.AES_OK
