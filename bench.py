@@ -357,6 +357,7 @@ def served(args, rank, local):
     gen = torch.Generator(device=dev).manual_seed(W.SEED_BASE + 4)
     pool = torch.randint(0, 256, (pool_n * 8 * MiB,), dtype=torch.uint8, device=dev, generator=gen)
     ring = torch.empty(ring_n * 8 * MiB, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)  # the served kernel runs on its own stream
     ctxs = [A.Context(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)]
     srv = A.Server(slots=1024, max_keys=64, idle_timeout_us=2_000_000)
     slots = [srv.key_register(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)]
@@ -419,6 +420,7 @@ def served(args, rank, local):
     gen = torch.Generator(device=dev).manual_seed(W.SEED_BASE + 5)
     src = torch.randint(0, 256, (n5 * big,), dtype=torch.uint8, device=dev, generator=gen)
     dst = torch.empty_like(src)
+    torch.cuda.synchronize(dev)
     g = W.rng(W.SEED_BASE + 7)
     keys5 = [W.random_bytes(g, 32) for _ in range(n5 // 1024)]
     ivs5 = W.random_bytes(g, 16 * n5).reshape(n5, 16)
@@ -573,6 +575,7 @@ def conflict_study(args, rank, local):
     gen = torch.Generator(device=dev).manual_seed(W.SEED_BASE + 11)
     src = torch.randint(0, 256, (handlers * stride,), dtype=torch.uint8, device=dev, generator=gen)
     dst = torch.empty_like(src)
+    torch.cuda.synchronize(dev)  # the served kernel runs on its own stream
     srv = A.Server(slots=256, max_keys=1, idle_timeout_us=2_000_000)
     names = {A.CDET_UNPROTECTED: "unprotected", A.CDET_LOCK: "coarse_lock", A.CDET_DETECT: "detect",
              A.CDET_ENFORCE: "enforce"}

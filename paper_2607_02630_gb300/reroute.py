@@ -278,11 +278,14 @@ def run_point(aes, torch, device, nbytes: int, server, key: bytes, bits: int = 1
     row = {"block_bytes": nbytes, "clients": nclients, "executor_threads": executor_threads}
     stream = torch.cuda.Stream(device=device)
     probe_dst = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    # the offloads run on streams of their own: wait for torch's initialisation
+    torch.cuda.synchronize(device)
     row["single_op_us"] = round(single_op_latency_us(aes, ctx, ivs[0], src[0].data_ptr(), probe_dst.data_ptr(),
                                                      nbytes, stream), 2)
     slot = server.key_register(key, bits) if "served" in modes else None
     for mode in modes:
         dst = torch.zeros((nclients, nbytes), dtype=torch.uint8, device=device)
+        torch.cuda.synchronize(device)
 
         def bufs(conn, dst=dst):
             return src[conn].data_ptr(), dst[conn].data_ptr()

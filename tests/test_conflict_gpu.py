@@ -31,6 +31,7 @@ def test_enforce_with_real_aes_offload(cuda, aes, ncpu):
         handlers, nbytes = 8, 64 << 10
         src = cuda.randint(0, 256, (handlers * nbytes,), dtype=cuda.uint8, device="cuda")
         dst = cuda.zeros_like(src)
+        cuda.cuda.synchronize()  # the served kernel runs on its own stream
         r = aes.conflict_run(aes.CDET_ENFORCE, handlers=handlers, requests=800, counters=8, server=srv,
                              key_slot=ks, buf_in=src, buf_out=dst, nbytes=nbytes)
         assert r["lost_updates"] == 0 and r["final_count"] == 800

@@ -74,6 +74,7 @@ def test_served_request_past_4gib(cuda, aes, ncpu, big):
     try:
         ks = srv.key_register(key.tobytes(), 128)
         dst.fill_(0xA5)
+        cuda.cuda.synchronize()  # the fill runs on torch's stream, the served kernel on its own
         t = srv.submit(ks, iv.tobytes(), src.data_ptr(), dst.data_ptr(), N)
         assert srv.wait(t, 30_000_000) == aes.AES_OK
         check(cuda, src, dst, key, 128, iv, ncpu)

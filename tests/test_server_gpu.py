@@ -31,10 +31,15 @@ def server(aes):
 
 
 def arena(torch, g, sizes):
+    """Payloads at 256-byte aligned offsets in one device buffer, and an
+    output buffer of 0xA5.  The fills run on torch's stream and the served
+    kernel on the server's own, so wait for them before submitting."""
     pad = [(n + 255) // 256 * 256 + 256 for n in sizes]
     offs = np.concatenate([[0], np.cumsum(pad)[:-1]]).astype(np.int64)
     payload = W.random_bytes(g, int(sum(pad)))
-    return payload, offs, to_dev(torch, payload), to_dev(torch, np.zeros(0, np.uint8), pad=int(sum(pad)))
+    src, dst = to_dev(torch, payload), to_dev(torch, np.zeros(0, np.uint8), pad=int(sum(pad)))
+    torch.cuda.synchronize()
+    return payload, offs, src, dst
 
 
 def test_served_results_match_oracle(cuda, aes, server, ncpu):
@@ -80,6 +85,7 @@ def test_same_result_alone_and_in_the_mix(cuda, aes, server):
         alone.append(to_host(dst[o: o + n]).copy())
     # in the mix: all submitted back to back, completing out of order
     dst.fill_(0xA5)
+    cuda.cuda.synchronize()  # the served kernel runs on its own stream
     order = list(g.permutation(len(sizes)))
     tickets = []
     for i in order:
@@ -175,6 +181,7 @@ def test_idle_exit_then_relaunch(cuda, aes, ncpu):
     data = W.random_bytes(g, 1 << 20)
     src = to_dev(cuda, data)
     dst = to_dev(cuda, np.zeros(0, np.uint8), pad=data.size)
+    cuda.cuda.synchronize()
     iv = W.random_bytes(g, 16)
     t = srv.submit(slot, iv.tobytes(), src, dst, data.size)
     assert srv.wait(t, WAIT_US) == aes.AES_OK
@@ -184,6 +191,7 @@ def test_idle_exit_then_relaunch(cuda, aes, ncpu):
     st = srv.stats()
     assert st["running"] == 0 and (st["kernel_status"] & 2), st  # exited on idle timeout
     dst.fill_(0)
+    cuda.cuda.synchronize()
     t = srv.submit(slot, iv.tobytes(), src, dst, data.size)
     assert srv.wait(t, WAIT_US) == aes.AES_OK
     assert srv.stats()["relaunches"] >= 1
@@ -441,6 +449,7 @@ def test_full_size_8mib_aes256_stream_sampled(cuda, aes, ncpu, budget_gib):
     gen = cuda.Generator(device="cuda").manual_seed(W.SEED_BASE + 5)
     src = cuda.randint(0, 256, (n5 * big,), dtype=cuda.uint8, device="cuda", generator=gen)
     dst = cuda.full((n5 * big,), 0xA5, dtype=cuda.uint8, device="cuda")
+    cuda.cuda.synchronize()  # the served kernel runs on its own stream
     g = W.rng(W.SEED_BASE + 7)
     keys5 = [W.random_bytes(g, 32) for _ in range(n5 // 1024)]
     ivs5 = W.random_bytes(g, 16 * n5).reshape(n5, 16)
