@@ -231,7 +231,7 @@ typedef struct {
     uint64_t hbm_budget;    /* bytes of payload in flight at most (in + out,
                                in-place counted once); 0 = unlimited */
     int ctas;               /* resident CTAs; 0 = SM count - 4 */
-    int threads;            /* CTA size, multiple of 32, 64..768; 0 = 768 (warp 0 dispatches) */
+    int threads;            /* CTA size, multiple of 32, 64..512; 0 = 512 (warp 0 dispatches) */
     int tile_blocks;        /* 16-byte blocks per tile: 64, 128 or a multiple of 256; 0 = per request (~512 tiles of 64..1024 blocks) */
     uint32_t idle_timeout_us; /* resident kernel exits after this long with no
                                  work (relaunched on the next submit); 0 = 200000 */

@@ -72,7 +72,7 @@ constexpr uint32_t kNotReady = 8;  // advance(): next request not ready (not an 
 constexpr uint32_t kFlagHostOut = 1;   // QEntry.flags: the output is pinned host memory
 constexpr uint32_t kFlagEmulated = 2;  // QEntry.flags: emulated offload, len = duration in ns
 constexpr uint64_t kMaxEmulatedNs = 10000000;
-constexpr int kMaxWarps = 24;   // CTA of at most 768 threads (80 registers each)
+constexpr int kMaxWarps = 16;   // CTA of at most 512 threads (128 registers each: round keys in registers)
 constexpr uint32_t kRing = 64;  // >= workers + prefetch
 // Tiles an agent keeps queued for its workers.  A deep queue rides through
 // the microseconds the global cursor needs to move from one request to the
@@ -478,11 +478,10 @@ __device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
     ring.exit_code = code;
 }
 
-__global__ void __launch_bounds__(768, 1) server_kernel(const __grid_constant__ SrvParams p)
+__global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ SrvParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ Ring ring;
-    __shared__ uint4 s_rk[kMaxWarps][15];  // round keys of each worker's current request
     if (threadIdx.x == 0) {
         ring.head = 0;
         ring.tail = 0;
@@ -502,7 +501,6 @@ __global__ void __launch_bounds__(768, 1) server_kernel(const __grid_constant__ 
         return;  // no CTA-wide barrier follows
     }
     const aestt::Lanes ln;
-    uint4 *w_rk = s_rk[warp];
     uint32_t cur_d = ~0u, cur_seq = ~0u, tg = 1, tp = 1;
     aesrt::BatchReq rq;
     for (;;) {
@@ -545,9 +543,6 @@ __global__ void __launch_bounds__(768, 1) server_kernel(const __grid_constant__ 
             tg = __ldcg(&rec->tile_groups);
             tp = __ldcg(&rec->tile_parts);
             __syncwarp();
-            if (lane <= rq.nr)
-                w_rk[lane] = __ldcg(rq.rk + lane);
-            __syncwarp();
             cur_d = d;
             cur_seq = seq;
         }
@@ -563,10 +558,12 @@ __global__ void __launch_bounds__(768, 1) server_kernel(const __grid_constant__ 
             uint64_t first, last;
             const uint32_t part = t % tp;
             aestile::tile_blocks_of(t / tp, tg, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
+            // round keys in registers: key slots are written once, before
+            // any request names them, so the read-only path is safe
             switch (rq.nr) {
-            case 10: aestile::run_tile_warp<10, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
-            case 12: aestile::run_tile_warp<12, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
-            default: aestile::run_tile_warp<14, 2>(rq, first, last, part, tp, smem, ln, w_rk); break;
+            case 10: aestile::run_tile_warp_regs<10, 2>(rq, first, last, part, tp, smem, ln); break;
+            case 12: aestile::run_tile_warp_regs<12, 2>(rq, first, last, part, tp, smem, ln); break;
+            default: aestile::run_tile_warp_regs<14, 2>(rq, first, last, part, tp, smem, ln); break;
             }
         }
         // Order this lane's output stores before the tile is counted: at
@@ -744,7 +741,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     const int slots = c.slots ? c.slots : 1024;
     const int max_keys = c.max_keys ? c.max_keys : 64;
     const int ctas = c.ctas ? c.ctas : std::max(1, st->nsm - 4);
-    const int threads = c.threads ? c.threads : 768;
+    const int threads = c.threads ? c.threads : 512;
     const int tile_blocks = c.tile_blocks;  // 0: chosen per request
     // warp 0 of each CTA is the agent, so at least one worker warp is needed
     if (slots < 1 || slots > kMaxSlots || max_keys < 1 || max_keys > (1 << 20) || ctas < 1 ||
