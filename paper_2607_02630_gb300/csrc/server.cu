@@ -411,6 +411,20 @@ __device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &st
     }
 }
 
+// Part `part` of `parts` of the single counter group [first, last) (or the
+// whole tile when parts == 1) of a request, done by the calling warp alone,
+// with the request's round keys in registers: key slots are written once,
+// before any request names them, so the read-only path is safe.
+template <int NR, int NB>
+__device__ __forceinline__ void run_part_regs(const aesrt::BatchReq &rq, uint64_t first, uint64_t last,
+                                              uint32_t part, uint32_t parts, const uint8_t *smem,
+                                              const aestt::Lanes &ln)
+{
+    const aestt::RkRegs<NR> rk(rq.rk);
+    aestile::xor_range<NR, NB>(rq.in, rq.out, rq.len, rq.iv_hi, rq.iv_lo, first, last, part, parts, parts, smem,
+                               ln, rk);
+}
+
 struct Ring {
     unsigned int head;               // positions reserved by workers (atomicAdd)
     volatile unsigned int tail;      // positions filled by the agent
@@ -558,12 +572,10 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
             uint64_t first, last;
             const uint32_t part = t % tp;
             aestile::tile_blocks_of(t / tp, tg, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
-            // round keys in registers: key slots are written once, before
-            // any request names them, so the read-only path is safe
             switch (rq.nr) {
-            case 10: aestile::run_tile_warp_regs<10, 2>(rq, first, last, part, tp, smem, ln); break;
-            case 12: aestile::run_tile_warp_regs<12, 2>(rq, first, last, part, tp, smem, ln); break;
-            default: aestile::run_tile_warp_regs<14, 2>(rq, first, last, part, tp, smem, ln); break;
+            case 10: run_part_regs<10, 2>(rq, first, last, part, tp, smem, ln); break;
+            case 12: run_part_regs<12, 2>(rq, first, last, part, tp, smem, ln); break;
+            default: run_part_regs<14, 2>(rq, first, last, part, tp, smem, ln); break;
             }
         }
         // Order this lane's output stores before the tile is counted: at

@@ -126,18 +126,6 @@ __device__ __forceinline__ void run_tile_warp_regs(const aesrt::BatchReq &rq, ui
     xor_range<NR, NB>(rq.in, rq.out, rq.len, rq.iv_hi, rq.iv_lo, first, last, 0, 1, 1, smem, ln, rk);
 }
 
-// Part `part` of `parts` of the single counter group [first, last) (or the
-// whole tile when parts == 1) of a request, done by the calling warp alone,
-// with the request's round keys loaded into registers.
-template <int NR, int NB>
-__device__ __forceinline__ void run_tile_warp_regs(const aesrt::BatchReq &rq, uint64_t first, uint64_t last,
-                                                   uint32_t part, uint32_t parts, const uint8_t *smem,
-                                                   const aestt::Lanes &ln)
-{
-    const aestt::RkRegs<NR> rk(rq.rk);
-    xor_range<NR, NB>(rq.in, rq.out, rq.len, rq.iv_hi, rq.iv_lo, first, last, part, parts, parts, smem, ln, rk);
-}
-
 // Part `part` of `parts` of the single counter group [first, last) of a
 // request, done by the calling warp alone (parts > 1 cuts a group's 8 blocks
 // per lane into parts, so one request spreads over more warps).
