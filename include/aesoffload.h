@@ -255,6 +255,11 @@ int offload_key_register(offload_server_t srv, const uint8_t *key, int bits, int
 
 /* Submit one request; never blocks on the GPU.  On AES_OK *ticket identifies
  * it for offload_poll.  Thread-safe (any number of submitter threads).
+ * Ordering: the resident kernel runs on the server's own stream and may read
+ * `in` and write `out` as soon as the call returns, so any GPU work that
+ * produces `in` or still touches `out` (a fill, a copy, a kernel on another
+ * stream) must be complete before the call -- e.g. synchronise that stream
+ * first.  `out` must not be touched again until offload_poll returns AES_OK.
  * Errors: AES_EAGAIN (no slot or budget free: back-pressure), AES_EINVAL
  * (bad key slot, null iv/in/out with len > 0), AES_EALIGN, AES_EOVERLAP,
  * AES_ETOOBIG (len > 16 GiB), AES_ESTOPPED, AES_ECUDA. */
