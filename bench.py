@@ -207,7 +207,7 @@ def reference_arm(args, ws, rank):
     w = W.batch_varlen(n=args.requests, seed=W.SEED_BASE + 3)
     per_step_s = args.reference_step_seconds
     if per_step_s is None:
-        per_step_s = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+        per_step_s = max(0.25, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
     idx, nbytes = oracle_sample(w, per_step_s, nthreads)
     for _ in range(args.warmup):
         run_oracle(w, idx[:1], nthreads)
