@@ -196,6 +196,28 @@ def run_oracle(w, idx, nthreads: int) -> float:
     return time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine
+    type), reported beside the oracle timings."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
+
+
 def workload_name(requests: int) -> str:
     return WORKLOAD if requests == 4096 else f"{requests} requests of: " + WORKLOAD
 
@@ -222,7 +244,8 @@ def reference_arm(args, ws, rank):
         "data": "synthetic", "config": {"workload": workload_name(args.requests),
                                         "global_batch": args.requests * args.gpus, "seq_len": None,
                                         "parallelism": f"replicas{args.gpus}"},
-        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": nthreads, "cpu": cpu_model(),
+                         "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -757,7 +780,8 @@ def main():
             nthreads = os.cpu_count() or 1
             idx, nbytes = oracle_sample(w, args.oracle_seconds, nthreads)
             secs = run_oracle(w, idx, nthreads)
-            cpu = {"value": round(nbytes / secs / 1e9, 6), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            cpu = {"value": round(nbytes / secs / 1e9, 6), "unit": UNIT, "cores": nthreads, "cpu": cpu_model(),
+                   "kind": "oracle",
                    "sample": f"first {len(idx)} of the 4096 requests ({nbytes / 1e6:.1f} MB), "
                              f"oracle_ctr_mt on {nthreads} threads, {secs:.1f} s"}
         line = {

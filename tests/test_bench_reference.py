@@ -29,6 +29,7 @@ def test_reference_arm_line():
     assert d["steps"] == 2 and d["warmup"] == 1
     assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert isinstance(d["cpu_baseline"]["cpu"], str) and d["cpu_baseline"]["cpu"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("32 requests of:")
 
