@@ -222,8 +222,31 @@ def workload_name(requests: int) -> str:
     return WORKLOAD if requests == 4096 else f"{requests} requests of: " + WORKLOAD
 
 
+def cpu_study(nthreads: int) -> dict:
+    """The oracle on single buffers of the configs' sizes, one thread and all
+    cores, AES-128 and AES-256 (payload GB/s; one timed run after a warm-up)."""
+    import oracle
+
+    oracle.build()
+    g = W.rng(W.SEED_BASE + 14)
+    rows = []
+    for n, threads in ((1 << 20, 1), (8 << 20, 1), (1 << 20, nthreads), (8 << 20, nthreads), (64 << 20, nthreads)):
+        data = W.random_bytes(g, n)
+        for bits in (128, 256):
+            key, iv = W.random_bytes(g, bits // 8), W.random_bytes(g, 16)
+            oracle.ctr_mt(key, bits, iv, data[: 1 << 16], threads)
+            t0 = time.perf_counter()
+            oracle.ctr_mt(key, bits, iv, data, threads)
+            secs = time.perf_counter() - t0
+            rows.append({"bytes": n, "bits": bits, "threads": threads, "gbs": round(n / secs / 1e9, 6)})
+    return {"cpu": cpu_model(), "cores": nthreads, "rows": rows}
+
+
 def reference_arm(args, ws, rank):
     if rank != 0:
+        return 0
+    if args.cpu_study:
+        print(json.dumps({"impl": "reference", "cpu_study": cpu_study(os.cpu_count() or 1)}), flush=True)
         return 0
     nthreads = os.cpu_count() or 1
     w = W.batch_varlen(n=args.requests, seed=W.SEED_BASE + 3)
@@ -649,6 +672,8 @@ def main():
     ap.add_argument("--requests", type=int, default=4096,
                     help="requests per step (4096 = the benchmark workload; fewer only for profiler captures)")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-study", action="store_true",
+                    help="with --impl reference: time the oracle on 1/8/64 MiB buffers, 1 thread and all cores")
     ap.add_argument("--reference-step-seconds", type=float, default=None,
                     help="CPU seconds of oracle work per --impl reference step (default: fit the run in ~150 s)")
     ap.add_argument("--sweep", action="store_true",
