@@ -127,6 +127,13 @@ __device__ __forceinline__ uint64_t gtime()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// Nanoseconds since t0, as a signed count: a timer that steps back reads as
+// negative (not idle) instead of wrapping to a huge unsigned difference.
+__device__ __forceinline__ int64_t since(uint64_t t0)
+{
+    return (int64_t)(gtime() - t0);
+}
 __device__ __forceinline__ void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
 {
     asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
@@ -157,7 +164,8 @@ struct StopCheck {
     __device__ __forceinline__ bool operator()(const unsigned int *flag)
     {
         const uint64_t now = gtime();
-        if (now < next)
+        const int64_t ahead = (int64_t)(next - now);
+        if (ahead > 0 && ahead <= 50000)  // read within the last 50 us (and the timer did not step back)
             return false;
         next = now + 50000;
         return ld_volatile(flag) != 0;
@@ -334,7 +342,7 @@ __device__ __noinline__ uint32_t advance(const SrvParams &p, uint32_t seq, uint6
                 r = kNotReady;
             else if (stop(p.stop))
                 r = kExitStop;
-            else if (gtime() - last_work > p.idle_ns)
+            else if (since(last_work) > (int64_t)p.idle_ns)
                 r = kExitIdle;
             if (r) {
                 atomicCAS(p.adv, (unsigned long long)nseq, (unsigned long long)seq);
@@ -403,7 +411,7 @@ __device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &st
                     break;  // the advancer gave up its role: compete for it again
                 if (stop(p.stop))
                     return kExitStop;
-                if (gtime() - last_work > p.idle_ns)
+                if (since(last_work) > (int64_t)p.idle_ns)
                     return kExitIdle;
                 __nanosleep(100);
             }
@@ -563,9 +571,13 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
         if (rq.pad & kFlagEmulated) {
             // emulated offload: hold this warp for rq.len ns (at most kMaxEmulatedNs)
             if (lane == 0) {
-                const uint64_t t_end = gtime() + rq.len;
-                while (gtime() < t_end)
+                const uint64_t t0 = gtime();
+                for (;;) {
+                    const int64_t el = since(t0);
+                    if (el >= (int64_t)rq.len || el < 0)  // done, or the timer stepped back
+                        break;
                     __nanosleep(256);
+                }
             }
             __syncwarp();
         } else {
