@@ -250,7 +250,12 @@ typedef struct {
 int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg);
 
 /* Expand `key` into resident key slot *slot_out (device kernel, FIPS-197
- * Sec. 5.2).  Thread-safe.  AES_ETOOBIG when all max_keys slots are used. */
+ * Sec. 5.2).  Thread-safe.  AES_ETOOBIG when all max_keys slots are used.
+ * May be called while the resident kernel runs: the expansion kernel runs on
+ * the SMs the resident kernel leaves free (ctas < SM count, the default), and
+ * the resident kernel reads round keys through L2, so a request submitted
+ * after this returns sees the new schedule.  With ctas = SM count the call
+ * returns after the resident kernel's next idle exit. */
 int offload_key_register(offload_server_t srv, const uint8_t *key, int bits, int *slot_out);
 
 /* Submit one request; never blocks on the GPU.  On AES_OK *ticket identifies

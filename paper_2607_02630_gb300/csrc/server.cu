@@ -419,16 +419,31 @@ __device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &st
     }
 }
 
+// Round keys in registers, read through L2 (coherent): the resident kernel
+// outlives key registrations, and adjacent 240-byte key slots share cache
+// lines, so a non-coherent (read-only path) copy of a line could predate a
+// key registered after it was cached.
+template <int NR>
+struct RkRegsL2 {
+    uint4 w[NR + 1];
+    __device__ __forceinline__ explicit RkRegsL2(const uint4 *g)
+    {
+#pragma unroll
+        for (int r = 0; r <= NR; ++r)
+            w[r] = __ldcg(g + r);
+    }
+    __device__ __forceinline__ uint4 get(int r) const { return w[r]; }
+};
+
 // Part `part` of `parts` of the single counter group [first, last) (or the
 // whole tile when parts == 1) of a request, done by the calling warp alone,
-// with the request's round keys in registers: key slots are written once,
-// before any request names them, so the read-only path is safe.
+// with the request's round keys in registers.
 template <int NR, int NB>
 __device__ __forceinline__ void run_part_regs(const aesrt::BatchReq &rq, uint64_t first, uint64_t last,
                                               uint32_t part, uint32_t parts, const uint8_t *smem,
                                               const aestt::Lanes &ln)
 {
-    const aestt::RkRegs<NR> rk(rq.rk);
+    const RkRegsL2<NR> rk(rq.rk);
     aestile::xor_range<NR, NB>(rq.in, rq.out, rq.len, rq.iv_hi, rq.iv_lo, first, last, part, parts, parts, smem,
                                ln, rk);
 }
@@ -624,6 +639,7 @@ struct offload_server_s {
     unsigned int *ctrl = nullptr;  // [0] stop, [1] kernel exit status
     // device memory
     uint8_t *dmem = nullptr;
+    uint8_t *key_stage = nullptr;  // 64 bytes in dmem: key + bits for one registration (under mu)
     SrvParams params{};
     cudaStream_t stream = nullptr;
     cudaStream_t setup = nullptr;
@@ -827,13 +843,16 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     std::memset(s->done, 0, sizeof(unsigned long long) * slots);
     std::memset(s->ctrl, 0, 64);
     // device: cursor, adv and disp each on a 4 KiB page of their own (every
-    // agent polls them), then disp_ring, recs, keys, key_nr
+    // agent polls them), then disp_ring, recs, keys, key_nr and the key
+    // staging area (registration allocates nothing: cudaFree would wait for
+    // the resident kernel to exit)
     const size_t off_adv = 4096, off_disp = 8192, off_slots = 12288;
     const size_t off_recs = 16384;
     static_assert(8 * kDispRing <= 4096, "disp_ring fits in its page");
     const size_t off_keys = off_recs + sizeof(SrvRec) * (size_t)slots;
     const size_t off_nr = off_keys + 240 * (size_t)max_keys;
-    const size_t dbytes = off_nr + sizeof(int) * (size_t)max_keys;
+    const size_t off_stage = (off_nr + sizeof(int) * (size_t)max_keys + 255) / 256 * 256;
+    const size_t dbytes = off_stage + 64;
     if ((e = cudaMalloc(&s->dmem, dbytes)))
         return fail("cudaMalloc(server)");
     if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)))
@@ -853,6 +872,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     P.recs = reinterpret_cast<SrvRec *>(s->dmem + off_recs);
     P.keys = reinterpret_cast<const uint4 *>(s->dmem + off_keys);
     P.key_nr = reinterpret_cast<const int *>(s->dmem + off_nr);
+    s->key_stage = s->dmem + off_stage;
     void *dp = nullptr;
     if ((e = cudaHostGetDevicePointer(&dp, s->queue, 0)))
         return fail("cudaHostGetDevicePointer");
@@ -902,17 +922,14 @@ int offload_key_register(offload_server_t s, const uint8_t *key, int bits, int *
         }
     if (slot < 0)
         return AES_ETOOBIG;
-    uint8_t *stage = nullptr;
-    cudaError_t e = cudaMalloc(&stage, 64);
-    if (e)
-        return e == cudaErrorMemoryAllocation ? AES_ENOMEM : cuda_fail(e, "cudaMalloc(key stage)");
+    uint8_t *stage = s->key_stage;
     uint8_t h[64] = {0};
     std::memcpy(h, key, bits / 8);
     const int32_t b = bits;
     std::memcpy(h + 32, &b, 4);
     const int nr = bits / 32 + 6;
     uint32_t *w = reinterpret_cast<uint32_t *>(const_cast<uint4 *>(s->params.keys + 15u * slot));
-    e = cudaMemcpyAsync(stage, h, 64, cudaMemcpyHostToDevice, s->setup);
+    cudaError_t e = cudaMemcpyAsync(stage, h, 64, cudaMemcpyHostToDevice, s->setup);
     if (!e)
         e = launch_key_expand(stage, reinterpret_cast<const int32_t *>(stage + 32), st->te0, w, 1, s->setup);
     if (!e)
@@ -920,7 +937,6 @@ int offload_key_register(offload_server_t s, const uint8_t *key, int bits, int *
                             cudaMemcpyHostToDevice, s->setup);
     if (!e)
         e = cudaStreamSynchronize(s->setup);
-    cudaFree(stage);
     if (e)
         return cuda_fail(e, "offload_key_register");
     s->key_used[slot] = 1;

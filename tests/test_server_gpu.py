@@ -67,6 +67,38 @@ def test_served_results_match_oracle(cuda, aes, server, ncpu):
     assert st["completed"] == len(sizes) and st["device_errors"] == 0
 
 
+def test_keys_registered_while_resident(cuda, aes, ncpu):
+    """Keys registered while the resident kernel runs: each new slot's first
+    round key shares a cache line with the slot before it, which the kernel
+    has just read.  Every request must use the key as registered."""
+    srv = aes.Server(slots=16, max_keys=8, ctas=8, tile_blocks=1024, idle_timeout_us=5_000_000)
+    try:
+        g = W.rng(67)
+        size = 256 << 10
+        keys = [(W.random_bytes(g, b // 8), b) for b in (128, 256, 192, 128, 256, 192, 128, 256)]
+        payload, offs, src, dst = arena(cuda, g, [size] * (2 * len(keys)))
+        ivs = [W.random_bytes(g, 16) for _ in range(2 * len(keys))]
+        relaunches = None
+        for k, (key, bits) in enumerate(keys):
+            slot = srv.key_register(key.tobytes(), bits)
+            assert slot == k
+            for i in (2 * k, 2 * k + 1):  # 16 tiles each: every CTA reads this slot
+                o = int(offs[i])
+                t = srv.submit(slot, ivs[i].tobytes(), src.data_ptr() + o, dst.data_ptr() + o, size)
+                assert srv.wait(t, WAIT_US) == aes.AES_OK
+            st = srv.stats()
+            if relaunches is None:
+                relaunches = st["relaunches"]
+            assert st["running"] == 1 and st["relaunches"] == relaunches, st  # still the same launch
+        out = to_host(dst)
+        for i in range(2 * len(keys)):
+            key, bits = keys[i // 2]
+            o = int(offs[i])
+            np.testing.assert_array_equal(out[o: o + size], oracle.ctr_mt(key, bits, ivs[i], payload[o: o + size], ncpu))
+    finally:
+        assert srv.close() == aes.AES_OK
+
+
 def test_same_result_alone_and_in_the_mix(cuda, aes, server):
     """Each request's bytes do not depend on what else is on the GPU."""
     g = W.rng(62)
