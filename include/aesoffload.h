@@ -80,7 +80,11 @@ typedef struct aes_ctx_s *aes_ctx_t;
 int aes_ctx_create(aes_ctx_t *out, const uint8_t *key, int bits);
 
 /* Release a context (NULL is a no-op).  The caller must ensure no work that
- * uses it is still queued or running.  Returns AES_OK. */
+ * uses it is still queued or running.  Returns AES_OK.  Frees device memory
+ * with cudaFree, which waits for the device's work in flight, a resident
+ * served kernel included (until its idle exit); create contexts up front
+ * and destroy them at shutdown when a server is running.  (aes_ctx_create
+ * frees nothing.) */
 int aes_ctx_destroy(aes_ctx_t ctx);
 
 /* Key size in bits, or AES_EINVAL for a NULL ctx. */

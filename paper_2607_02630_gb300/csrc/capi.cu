@@ -197,19 +197,17 @@ int aes_ctx_create(aes_ctx_t *out, const uint8_t *key, int bits)
     ctx->device = st->device;
     ctx->bits = bits;
     ctx->nr = bits / 32 + 6;
-    // staging: 32 key bytes + 4-byte key size, then the 60-word schedule
-    uint8_t *stage = nullptr;
-    cudaError_t e = cudaMalloc(&stage, 64);
+    // one allocation: the 60-word schedule, then (at byte 256) the staging
+    // area for the expansion kernel's input, 32 key bytes + 4-byte key size.
+    // No temporary buffer is freed here: cudaFree waits for the device to go
+    // idle, which a resident served kernel may postpone.
+    static_assert(kMaxRoundKeyWords * sizeof(uint32_t) <= 256, "schedule fits below the stage");
+    cudaError_t e = cudaMalloc(&ctx->d_rk, 256 + 64);
     if (e) {
-        delete ctx;
-        return e == cudaErrorMemoryAllocation ? AES_ENOMEM : cuda_fail(e, "cudaMalloc(stage)");
-    }
-    e = cudaMalloc(&ctx->d_rk, kMaxRoundKeyWords * sizeof(uint32_t));
-    if (e) {
-        cudaFree(stage);
         delete ctx;
         return e == cudaErrorMemoryAllocation ? AES_ENOMEM : cuda_fail(e, "cudaMalloc(rk)");
     }
+    uint8_t *stage = reinterpret_cast<uint8_t *>(ctx->d_rk) + 256;
     uint8_t hstage[64] = {0};
     std::memcpy(hstage, key, bits / 8);
     const int32_t b32 = bits;
@@ -220,7 +218,6 @@ int aes_ctx_create(aes_ctx_t *out, const uint8_t *key, int bits)
     if (!e) e = cudaMemcpyAsync(ctx->h_rk, ctx->d_rk, sizeof(ctx->h_rk), cudaMemcpyDeviceToHost,
                                 st->setup);
     if (!e) e = cudaStreamSynchronize(st->setup);
-    cudaFree(stage);
     if (e) {
         cudaFree(ctx->d_rk);
         delete ctx;
