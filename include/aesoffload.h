@@ -244,7 +244,10 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, rejected_eagain, device_errors, relaunches;
     uint64_t bytes_completed;
-    uint32_t kernel_status;    /* last exit status of the resident kernel */
+    uint32_t kernel_status;    /* exit reasons (1 stop, 2 idle, 4 error) raised by
+                                  the CTAs of the current launch, or of the
+                                  last one once it has ended; 0 while every
+                                  CTA of a running launch is resident */
     int running;               /* resident kernel currently launched */
 } offload_stats_t;
 

@@ -405,8 +405,13 @@ __device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &st
                 return r;
         } else {
             for (uint32_t spin = 0;; ++spin) {
-                if ((uint32_t)(ld_relaxed_gpu(p.cursor) >> 36) != seq)
+                if ((uint32_t)(ld_relaxed_gpu(p.cursor) >> 36) != seq) {
+                    // the server is working even if this CTA's claims keep
+                    // losing: idle means no new request anywhere, so a CTA
+                    // does not exit under light load while others serve
+                    last_work = gtime();
                     break;
+                }
                 if ((spin & 7) == 7 && (uint32_t)ld_relaxed_gpu(p.adv) == seq)
                     break;  // the advancer gave up its role: compete for it again
                 if (stop(p.stop))
@@ -1057,7 +1062,7 @@ int offload_server_stats(offload_server_t s, offload_stats_t *out)
     out->bytes_completed = s->n_bytes.load();
     const cudaError_t q = cudaStreamQuery(s->stream);
     out->running = q == cudaErrorNotReady ? 1 : 0;
-    out->kernel_status = out->running ? s->last_status : s->ctrl[1];
+    out->kernel_status = __atomic_load_n(&s->ctrl[1], __ATOMIC_ACQUIRE);
     return AES_OK;
 }
 

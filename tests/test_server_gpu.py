@@ -231,6 +231,37 @@ def test_idle_exit_then_relaunch(cuda, aes, ncpu):
     assert srv.close() == aes.AES_OK
 
 
+def test_light_load_keeps_every_cta_resident(cuda, aes, ncpu):
+    """Requests of a few tiles, one every 10 ms: each is claimed by one or
+    two of the 32 CTAs, so most CTAs go far longer than the idle timeout
+    without a tile of their own.  Idle means no new request anywhere, so no
+    CTA may exit while requests keep coming (kernel_status stays 0)."""
+    srv = aes.Server(slots=8, max_keys=1, ctas=32, tile_blocks=64, idle_timeout_us=150_000)
+    try:
+        g = W.rng(68)
+        key = W.random_bytes(g, 16)
+        slot = srv.key_register(key.tobytes(), 128)
+        n, size = 60, 1024
+        payload, offs, src, dst = arena(cuda, g, [size] * n)
+        ivs = [W.random_bytes(g, 16) for _ in range(n)]
+        t_end = time.time()
+        for i in range(n):
+            o = int(offs[i])
+            t = srv.submit(slot, ivs[i].tobytes(), src.data_ptr() + o, dst.data_ptr() + o, size)
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+            time.sleep(0.01)
+        t_end = time.time() - t_end
+        st = srv.stats()
+        assert t_end > 0.6  # at least four idle timeouts of light load
+        assert st["running"] == 1 and st["relaunches"] == 0 and st["kernel_status"] == 0, st
+        out = to_host(dst)
+        for i in range(n):
+            o = int(offs[i])
+            np.testing.assert_array_equal(out[o: o + size], oracle.ctr(key, 128, ivs[i], payload[o: o + size]))
+    finally:
+        assert srv.close() == aes.AES_OK
+
+
 def test_stop_with_work_in_flight(cuda, aes):
     srv = aes.Server(slots=32, max_keys=2, ctas=16, idle_timeout_us=2_000_000)
     slot = srv.key_register(bytes(16), 128)
