@@ -52,7 +52,6 @@ namespace {
 using clk = std::chrono::steady_clock;
 
 constexpr size_t kStack = 256 * 1024;
-constexpr int kMaxDirty = 64;
 
 struct Fiber {
     ucontext_t ctx;
@@ -66,8 +65,7 @@ struct Fiber {
     uint64_t snapshot = 0;      // version clock when it last parked
     uint64_t ticket = 0;        // offload in flight (server)
     clk::time_point deadline;   // offload in flight (host timer)
-    int dirty[kMaxDirty];
-    int ndirty = 0;
+    int dirty_lo = 0, dirty_hi = -1;  // pages this handler unprotected: within [lo, hi]
 };
 
 struct Run {
@@ -98,11 +96,16 @@ uint64_t *counter_ptr(Run &r, int c)
     return reinterpret_cast<uint64_t *>(r.region + (size_t)pg * (size_t)r.page + 64u * (size_t)slot);
 }
 
+// Only the running handler's pages are ever writable (every other page is
+// read-only whenever another handler runs), so one call over the range that
+// spans its unprotected pages restores the invariant, however many they are.
 void protect_dirty(Run &r, Fiber &f)
 {
-    for (int i = 0; i < f.ndirty; ++i)
-        mprotect(r.region + (size_t)f.dirty[i] * (size_t)r.page, (size_t)r.page, PROT_READ);
-    f.ndirty = 0;
+    if (f.dirty_hi >= f.dirty_lo)
+        mprotect(r.region + (size_t)f.dirty_lo * (size_t)r.page,
+                 (size_t)(f.dirty_hi - f.dirty_lo + 1) * (size_t)r.page, PROT_READ);
+    f.dirty_lo = 0;
+    f.dirty_hi = -1;
 }
 
 void on_fault(int sig, siginfo_t *si, void *uc)
@@ -127,8 +130,13 @@ void on_fault(int sig, siginfo_t *si, void *uc)
     }
     r->page_version[(size_t)p] = ++r->clock;
     mprotect(r->region + (size_t)p * (size_t)r->page, (size_t)r->page, PROT_READ | PROT_WRITE);
-    if (f.ndirty < kMaxDirty)
-        f.dirty[f.ndirty++] = p;
+    if (f.dirty_hi < f.dirty_lo) {
+        f.dirty_lo = p;
+        f.dirty_hi = p;
+    } else {
+        f.dirty_lo = p < f.dirty_lo ? p : f.dirty_lo;
+        f.dirty_hi = p > f.dirty_hi ? p : f.dirty_hi;
+    }
 }
 
 bool offload_done(Run &r, Fiber &f)
