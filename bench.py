@@ -405,7 +405,8 @@ def served(args, rank, local):
     ring = torch.empty(ring_n * 8 * MiB, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize(dev)  # the served kernel runs on its own stream
     ctxs = [A.Context(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)]
-    srv = A.Server(slots=1024, max_keys=64, idle_timeout_us=2_000_000)
+    cm = args.claim_mode
+    srv = A.Server(slots=1024, max_keys=64, idle_timeout_us=2_000_000, claim_mode=cm)
     slots = [srv.key_register(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)]
     reqs = np.zeros(n, dtype=A.drive_dtype())
     reqs["iv"] = ivs
@@ -445,7 +446,7 @@ def served(args, rank, local):
                          "gbs": round(res_pc["bytes"] / res_pc["elapsed_s"] / 1e9, 2), "errors": res_pc["errors"]}})
     srv.close()
     # the same requests on a server cut for throughput (fixed 1024-block tiles)
-    srv = A.Server(slots=1024, max_keys=64, idle_timeout_us=2_000_000, tile_blocks=1024)
+    srv = A.Server(slots=1024, max_keys=64, idle_timeout_us=2_000_000, tile_blocks=1024, claim_mode=cm)
     slots_t = [srv.key_register(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)]
     tput_reqs = served_reqs.copy()
     tput_reqs["key_slot"] = np.array(slots_t)[key_idx]
@@ -456,6 +457,7 @@ def served(args, rank, local):
     sat_t = {"req_per_s": round(n / res_t["elapsed_s"], 1), "gbs": round(total / res_t["elapsed_s"] / 1e9, 2),
              "errors": res_t["errors"], "config": "tile_blocks=1024"}
     out["open_loop"] = {"requests_per_rate": n, "payload_bytes_per_rate": total, "submitter_threads": 8,
+                        "claim_mode": cm,
                         "saturation_served": sat, "saturation_served_tile1024": sat_t,
                         "saturation_per_call": sat_pc, "rates": rates}
     del pool, ring, ctxs
@@ -472,7 +474,7 @@ def served(args, rank, local):
     ivs5 = W.random_bytes(g, 16 * n5).reshape(n5, 16)
     stream = {}
     for budget in (20 << 30, 2 << 30):
-        srv = A.Server(slots=512, max_keys=4, hbm_budget=budget, idle_timeout_us=2_000_000)
+        srv = A.Server(slots=512, max_keys=4, hbm_budget=budget, idle_timeout_us=2_000_000, claim_mode=cm)
         ks = [srv.key_register(k.tobytes(), 256) for k in keys5]
         r5 = np.zeros(n5, dtype=A.drive_dtype())
         r5["key_slot"] = np.array(ks)[np.arange(n5) // 1024]
@@ -700,6 +702,8 @@ def main():
     ap.add_argument("--served", action="store_true",
                     help="served-mode studies: open-loop Poisson rates and the large 8 MiB stream")
     ap.add_argument("--served-requests", type=int, default=20000)
+    ap.add_argument("--claim-mode", type=int, default=0, choices=[0, 1],
+                    help="served studies: 0 = global claim cursor, 1 = per-request claim words")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

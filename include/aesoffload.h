@@ -239,6 +239,11 @@ typedef struct {
     int tile_blocks;        /* 16-byte blocks per tile: 64, 128 or a multiple of 256; 0 = per request (~512 tiles of 64..1024 blocks) */
     uint32_t idle_timeout_us; /* resident kernel exits after this long with no
                                  work (relaunched on the next submit); 0 = 200000 */
+    int claim_mode;         /* how agents claim tiles: 0 = one global cursor
+                               moved from request to request (default);
+                               1 = per-request claim words that agents walk in
+                               sequence order, several requests cut at once
+                               (experimental: not yet measured) */
 } offload_cfg_t;
 
 typedef struct {

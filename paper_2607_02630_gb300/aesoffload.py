@@ -64,7 +64,7 @@ class BatchOpts(ctypes.Structure):
 class ServerCfg(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_keys", ctypes.c_int), ("hbm_budget", ctypes.c_uint64),
                 ("ctas", ctypes.c_int), ("threads", ctypes.c_int), ("tile_blocks", ctypes.c_int),
-                ("idle_timeout_us", ctypes.c_uint32)]
+                ("idle_timeout_us", ctypes.c_uint32), ("claim_mode", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -335,8 +335,8 @@ class Server:
     """Served mode: a resident kernel polling mapped descriptors (offload_*)."""
 
     def __init__(self, slots=0, max_keys=0, hbm_budget=0, ctas=0, threads=0, tile_blocks=0,
-                 idle_timeout_us=0):
-        cfg = ServerCfg(slots, max_keys, hbm_budget, ctas, threads, tile_blocks, idle_timeout_us)
+                 idle_timeout_us=0, claim_mode=0):
+        cfg = ServerCfg(slots, max_keys, hbm_budget, ctas, threads, tile_blocks, idle_timeout_us, claim_mode)
         h = ctypes.c_void_p()
         _check(lib().offload_server_create(ctypes.byref(h), ctypes.byref(cfg)), "offload_server_create")
         self.handle = h.value

@@ -1,0 +1,698 @@
+// served_protocol.cuh -- the request protocol of the served kernel: queue
+// entry and record layouts, dispatch of queued requests into device
+// records, the two ways agents claim tiles (one global cursor moved from
+// request to request; per-request claim words), and the completion of a
+// request's last tile.
+//
+// The same source compiles for the device (nvcc: PTX memory operations at
+// the scopes the protocol needs) and for the host (GCC atomics on plain
+// memory).  Host threads standing in for the resident CTAs can then run the
+// protocol's logic -- every tile claimed once, every request completed once,
+// slot reuse, idle exits and relaunches -- without a GPU.  A host run checks
+// logic only: CPUs order memory differently from the GPU.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+#ifdef __CUDACC__
+#define SRV_INLINE __device__ __forceinline__
+#define SRV_NOINLINE __device__ __noinline__
+#define SRV_FN __device__
+#else
+#include <chrono>
+#include <thread>
+#define SRV_INLINE inline
+#define SRV_NOINLINE inline
+#define SRV_FN inline
+#endif
+
+namespace srvp {
+
+constexpr uint32_t kSeqMask = (1u << 28) - 1;
+constexpr uint32_t kTileBits = 20;
+constexpr uint32_t kTileMask = (1u << kTileBits) - 1;
+constexpr uint32_t kMaxTiles = (1u << kTileBits) - 16384;  // headroom for batched exhausted claims
+constexpr int kMaxSlots = 65535;
+constexpr uint32_t kExitStop = 1, kExitIdle = 2, kExitError = 4;
+constexpr uint32_t kNotReady = 8;  // advance(): next request not ready (not an exit reason)
+constexpr uint32_t kFlagHostOut = 1;   // QEntry.flags: the output is pinned host memory
+constexpr uint32_t kFlagEmulated = 2;  // QEntry.flags: emulated offload, len = duration in ns
+constexpr uint64_t kMaxEmulatedNs = 10000000;
+constexpr int kMaxWarps = 16;   // CTA of at most 512 threads (128 registers each: round keys in registers)
+constexpr uint32_t kRing = 64;  // >= workers + prefetch
+// Tiles an agent keeps queued for its workers.  A deep queue rides through
+// the microseconds the global cursor needs to move from one request to the
+// next (8 MiB AES-256 stream: 440 GB/s with 1 queued tile, 664 with 16).
+constexpr uint32_t kPrefetch = 16;
+constexpr uint32_t kMaxClaim = 4;    // tiles per claim: spreads a request over many SMs
+constexpr uint32_t kLookahead = 8;   // requests validated ahead of the cursor
+constexpr uint32_t kDispRing = 64;   // > kLookahead
+constexpr uint32_t kDispatchBatch = 4;  // queue entries read per round trip over the host link
+// Per-request claims (claim_mode 1): a request's claim word holds its
+// sequence number above a 36-bit tile counter, so claims that overshoot the
+// tile count never reach the sequence bits; disp carries a busy bit while
+// one agent dispatches.
+constexpr uint32_t kClaimShift = 36;
+constexpr uint64_t kClaimTileMask = (1ull << kClaimShift) - 1;
+constexpr uint64_t kDispBusy = 1ull << 40;
+
+struct QEntry {  // 64 bytes, host-written, tag last
+    uint64_t tag;  // sequence number + 1
+    uint64_t in, out, len, iv_hi, iv_lo, gen;
+    uint32_t key_slot;
+    uint16_t desc;   // slot index d
+    uint16_t flags;  // kFlagHostOut, kFlagEmulated
+};
+static_assert(sizeof(QEntry) == 64, "QEntry layout");
+
+struct SrvRec {  // device-only, 128 bytes
+    aesrt::BatchReq rq;             // rq.pad holds the flags
+    unsigned long long seq_ntiles;  // (seq << 20) | ntiles, written after the rest
+    unsigned long long gen;
+    unsigned int tile_groups;       // this request's tile: tile_groups groups, or
+    unsigned int tile_parts;        // 1/tile_parts of one group
+    unsigned int done_tiles;
+    unsigned int pad0;
+    unsigned long long claim;       // per-request claims: (seq << 36) | next tile
+    unsigned int pad[6];
+};
+static_assert(offsetof(SrvRec, tile_groups) % 8 == 0, "tile shape words are 8-byte aligned");
+static_assert(offsetof(SrvRec, claim) % 8 == 0, "claim word is 8-byte aligned");
+static_assert(sizeof(SrvRec) == 128, "SrvRec layout");
+
+struct SrvParams {
+    unsigned long long *cursor;
+    unsigned long long *adv;
+    unsigned long long *disp;      // next sequence number to dispatch (validate into recs)
+    unsigned long long *disp_ring; // kDispRing: ring_entry() of dispatched request s at s % kDispRing
+    SrvRec *recs;
+    const uint4 *keys;          // max_keys x 15 round keys
+    const int *key_nr;          // max_keys; 0 = unregistered
+    const QEntry *queue;        // mapped
+    unsigned long long *done;   // mapped
+    const unsigned int *stop;   // mapped
+    unsigned int *kstatus;      // mapped
+    const uint32_t *te0;
+    uint32_t qmask, max_keys, tile_blocks, nslots;  // tile_blocks 0 = chosen per request
+    uint64_t idle_ns, max_len;
+};
+
+// ---- memory operations ----------------------------------------------------
+#ifdef __CUDACC__
+SRV_INLINE uint64_t gtime()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+SRV_INLINE void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
+{
+    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+SRV_INLINE uint64_t ld_relaxed_gpu(const unsigned long long *p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+SRV_INLINE void st_relaxed_gpu(unsigned long long *p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+SRV_INLINE void st_release_sys(unsigned long long *p, uint64_t v)
+{
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+SRV_INLINE uint32_t ld_volatile(const unsigned int *p)
+{
+    return *reinterpret_cast<const volatile unsigned int *>(p);
+}
+SRV_INLINE uint64_t ld_relaxed_sys(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+SRV_INLINE void fence_acq_rel_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
+SRV_INLINE void fence_gpu() { __threadfence(); }
+SRV_INLINE void fence_sys() { __threadfence_system(); }
+SRV_INLINE void nap(unsigned ns) { __nanosleep(ns); }
+template <class T>
+SRV_INLINE T ld_cg(const T *p)
+{
+    return __ldcg(p);
+}
+SRV_INLINE unsigned long long atom_add(unsigned long long *p, unsigned long long v) { return atomicAdd(p, v); }
+SRV_INLINE unsigned int atom_add(unsigned int *p, unsigned int v) { return atomicAdd(p, v); }
+SRV_INLINE unsigned long long atom_cas(unsigned long long *p, unsigned long long c, unsigned long long v)
+{
+    return atomicCAS(p, c, v);
+}
+SRV_INLINE unsigned long long atom_exch(unsigned long long *p, unsigned long long v) { return atomicExch(p, v); }
+#else
+inline uint64_t gtime()
+{
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+inline void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
+{
+    a = __atomic_load_n(p, __ATOMIC_RELAXED);
+    b = __atomic_load_n(p + 1, __ATOMIC_RELAXED);
+}
+inline uint64_t ld_relaxed_gpu(const unsigned long long *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
+inline void st_relaxed_gpu(unsigned long long *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELAXED); }
+inline void st_release_sys(unsigned long long *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+inline uint32_t ld_volatile(const unsigned int *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
+inline uint64_t ld_relaxed_sys(const uint64_t *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
+inline void fence_acq_rel_sys() { __atomic_thread_fence(__ATOMIC_ACQ_REL); }
+inline void fence_gpu() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
+inline void fence_sys() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
+inline void nap(unsigned) { std::this_thread::yield(); }
+template <class T>
+inline T ld_cg(const T *p)
+{
+    return __atomic_load_n(p, __ATOMIC_RELAXED);
+}
+inline unsigned long long atom_add(unsigned long long *p, unsigned long long v)
+{
+    return __atomic_fetch_add(p, v, __ATOMIC_RELAXED);
+}
+inline unsigned int atom_add(unsigned int *p, unsigned int v) { return __atomic_fetch_add(p, v, __ATOMIC_RELAXED); }
+inline unsigned long long atom_cas(unsigned long long *p, unsigned long long c, unsigned long long v)
+{
+    __atomic_compare_exchange_n(p, &c, v, false, __ATOMIC_RELAXED, __ATOMIC_RELAXED);
+    return c;
+}
+inline unsigned long long atom_exch(unsigned long long *p, unsigned long long v)
+{
+    return __atomic_exchange_n(p, v, __ATOMIC_RELAXED);
+}
+#endif
+
+// Nanoseconds since t0, as a signed count: a timer that steps back reads as
+// negative (not idle) instead of wrapping to a huge unsigned difference.
+SRV_INLINE int64_t since(uint64_t t0)
+{
+    return (int64_t)(gtime() - t0);
+}
+
+// The stop flag lives in host memory (one NVLink-C2C round trip per read),
+// so spinning loops look at it at most every 50 us.
+struct StopCheck {
+    uint64_t next = 0;
+    SRV_INLINE bool operator()(const unsigned int *flag)
+    {
+        const uint64_t now = gtime();
+        const int64_t ahead = (int64_t)(next - now);
+        if (ahead > 0 && ahead <= 50000)  // read within the last 50 us (and the timer did not step back)
+            return false;
+        next = now + 50000;
+        return ld_volatile(flag) != 0;
+    }
+};
+
+// Entry of the dispatch ring for request k: sequence number (28 bits), slot
+// d (16 bits; 0xffff marks a queue entry the host never writes) and tile
+// count (20 bits).  It is stored after the request's record is complete, so
+// an entry that carries k is all the advancer needs to move the cursor.
+SRV_INLINE uint64_t ring_entry(uint32_t k, uint32_t d, uint32_t ntiles)
+{
+    return ((uint64_t)k << 36) | ((uint64_t)d << kTileBits) | ntiles;
+}
+
+// Dispatch, in sequence order, up to n_max requests starting at k0 (the
+// value of disp the caller saw) whose queue entries are present: their tags
+// are read in one round trip over the host link and the requests claimed
+// with one CAS on disp (one dispatcher per request); then the entries are
+// read (acquire pattern: relaxed tag loads, then a system-scope fence) and
+// validated into recs[d], and finally their dispatch-ring entries are
+// published.  A request without tiles is completed here.  Returns the number
+// of requests dispatched (0: k0 not queued yet, or someone else took it) and,
+// in *first, the ring entry of request k0.
+// PER_REQ (claim_mode 1): the caller holds the dispatch lock (disp = k0 |
+// kDispBusy), so there is no CAS here, and each record's claim word is set
+// with its tile count.
+template <bool PER_REQ>
+SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, uint64_t *first = nullptr)
+{
+    uint32_t m = 0;
+    {
+        uint64_t tag[kDispatchBatch];
+#pragma unroll
+        for (uint32_t i = 0; i < kDispatchBatch; ++i)
+            tag[i] = i < n_max ? ld_relaxed_sys(&p.queue[(k0 + i) & p.qmask].tag) : 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kDispatchBatch; ++i)
+            if (m == i && i < n_max && (uint32_t)(tag[i] & kSeqMask) == ((k0 + i + 1) & kSeqMask))
+                m = i + 1;
+    }
+    if (m == 0)
+        return 0;
+    fence_acq_rel_sys();
+    if (!PER_REQ && atom_cas(p.disp, (unsigned long long)k0, (unsigned long long)((k0 + m) & kSeqMask)) != k0)
+        return 0;
+    uint64_t x[kDispatchBatch][7];
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+        if (i < m) {
+            const uint64_t *e = reinterpret_cast<const uint64_t *>(p.queue + ((k0 + i) & p.qmask));
+            uint64_t unused;
+            ld_volatile_v2(e + 0, unused, x[i][0]);
+            ld_volatile_v2(e + 2, x[i][1], x[i][2]);
+            ld_volatile_v2(e + 4, x[i][3], x[i][4]);
+            ld_volatile_v2(e + 6, x[i][5], x[i][6]);
+            (void)unused;
+        }
+    }
+    uint64_t ent[kDispatchBatch] = {};
+    uint32_t done_word[kDispatchBatch] = {};  // status for a request completed here, else 0
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+        if (i >= m)
+            continue;
+        const uint32_t k = (k0 + i) & kSeqMask;
+        const uint64_t in = x[i][0], out = x[i][1], len = x[i][2], iv_hi = x[i][3], iv_lo = x[i][4];
+        const uint32_t ks = (uint32_t)x[i][6];
+        const uint32_t d = (uint32_t)(x[i][6] >> 32) & 0xffffu;
+        const uint32_t flags = (uint32_t)(x[i][6] >> 48);
+        done_word[i] = 0;
+        if (d >= p.nslots) {  // the host never writes such an entry; the advancer stops on it
+            ent[i] = ring_entry(k, 0xffffu, 0);
+            continue;
+        }
+        int nr = 0;
+        if (ks < p.max_keys)
+            nr = ld_cg(p.key_nr + ks);
+        bool ok = (nr == 10 || nr == 12 || nr == 14) && len <= p.max_len;
+        if (ok && len)
+            ok = in && out && !((in | out) & 15u);
+        uint32_t ntiles = 0, tg = 1, tp = 1;
+        const bool emulated = (flags & kFlagEmulated) != 0;
+        if (emulated) {  // one tile that holds a worker warp for len ns; no key, no payload
+            ok = len <= kMaxEmulatedNs;
+            ntiles = ok ? 1u : 0u;
+            nr = 0;
+        } else if (ok && len) {
+            // tiles are runs of tg whole 256-block counter groups, or (tp > 1)
+            // equal parts of one group.  Unless fixed by the server config, a
+            // request is cut into about 512 tiles of 64..1024 blocks: short
+            // requests spread over many warps, long ones keep claims rare.
+            const uint64_t nb = (len + 15) >> 4;
+            const uint64_t groups = (((iv_lo & 255u) + nb - 1) >> 8) + 1;
+            uint32_t tb = p.tile_blocks;
+            if (!tb) {
+                tb = 64;
+                while (tb < 1024 && (uint64_t)tb * 512 < nb)
+                    tb <<= 1;
+            }
+            if (tb >= 256)
+                tg = tb / 256;
+            else
+                tp = 256 / tb;
+            ntiles = (uint32_t)((groups + tg - 1) / tg * tp);
+        }
+        SrvRec *rec = p.recs + d;
+        rec->rq.in = reinterpret_cast<const uint4 *>(in);
+        rec->rq.out = reinterpret_cast<uint4 *>(out);
+        rec->rq.len = len;
+        rec->rq.iv_hi = iv_hi;
+        rec->rq.iv_lo = iv_lo;
+        rec->rq.rk = p.keys + 15u * (ok && !emulated ? ks : 0u);
+        rec->rq.nr = (uint32_t)nr;
+        rec->rq.pad = flags;
+        rec->gen = x[i][5];
+        rec->done_tiles = 0;
+        rec->tile_groups = tg;
+        rec->tile_parts = tp;
+        ent[i] = ring_entry(k, d, ntiles);
+        if (ntiles == 0)
+            done_word[i] = ok ? 1u : 2u;
+    }
+    fence_gpu();
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+        const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
+        if (i < m && d != 0xffffu) {
+            st_relaxed_gpu(&p.recs[d].seq_ntiles, ((ent[i] >> 36) << kTileBits) | (ent[i] & kTileMask));
+            if (PER_REQ)
+                st_relaxed_gpu(&p.recs[d].claim, (ent[i] >> 36) << kClaimShift);
+        }
+    }
+    fence_gpu();
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i)
+        if (i < m)
+            st_relaxed_gpu(p.disp_ring + ((k0 + i) % kDispRing), ent[i]);
+#pragma unroll
+    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+        if (i < m && done_word[i]) {
+            const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
+            fence_sys();
+            st_release_sys(p.done + d, (x[i][5] << 2) | done_word[i]);
+        }
+    }
+    if (first)
+        *first = ent[0];
+    return m;
+}
+
+// Elected advancer (adv has been moved from seq to seq + 1): move the cursor
+// to request seq + 1 once its dispatch-ring entry is published (dispatching
+// it, with what is queued behind it, if it is next in line), step over
+// requests without tiles, and dispatch up to kLookahead requests ahead.
+// With block == false the role is handed back at once (kNotReady) when the
+// next request is not ready.  Returns 0, kNotReady or an exit code (after
+// handing the role back).
+SRV_NOINLINE uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_work, StopCheck &stop,
+                                        bool block)
+{
+    for (;;) {
+        const uint32_t nseq = (seq + 1) & kSeqMask;
+        uint64_t e = 0;
+        for (;;) {
+            e = ld_relaxed_gpu(p.disp_ring + (nseq % kDispRing));
+            if ((uint32_t)(e >> 36) == nseq)
+                break;  // dispatched and published
+            const uint32_t dsp = (uint32_t)ld_relaxed_gpu(p.disp);
+            if (dsp == nseq && dispatch<false>(p, nseq, kLookahead + 1, &e))
+                break;  // dispatched it here: e is its ring entry
+            uint32_t r = 0;
+            if (!block)
+                r = kNotReady;
+            else if (stop(p.stop))
+                r = kExitStop;
+            else if (since(last_work) > (int64_t)p.idle_ns)
+                r = kExitIdle;
+            if (r) {
+                atom_cas(p.adv, (unsigned long long)nseq, (unsigned long long)seq);
+                return r;
+            }
+            nap(32);
+        }
+        const uint32_t d = (uint32_t)(e >> kTileBits) & 0xffffu;
+        if (d >= p.nslots)
+            return kExitError;
+        // Only the elected advancer changes the sequence number; claims that
+        // raced with it only added to the tile count of the old request.
+        atom_exch(p.cursor, ((unsigned long long)nseq << 36) | ((unsigned long long)d << kTileBits));
+        last_work = gtime();
+        const uint32_t k = (uint32_t)ld_relaxed_gpu(p.disp);
+        const uint32_t ahead = (k - nseq) & kSeqMask;
+        if (ahead <= kLookahead)
+            dispatch<false>(p, k, kLookahead + 1 - ahead);
+        if (e & kTileMask)
+            return 0;
+        // nothing to claim in nseq: step over it, unless another agent
+        // (which saw the empty request) already took that role
+        if (atom_cas(p.adv, (unsigned long long)nseq, (unsigned long long)((nseq + 1) & kSeqMask)) != nseq)
+            return 0;
+        seq = nseq;
+    }
+}
+
+// Claim up to `want` tiles of the current request (the agent of a CTA).
+// Returns 0 with the tiles [*t0, *t1) of slot *d and its sequence number, or
+// an exit code.
+SRV_FN uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &stop, uint32_t want,
+                          uint32_t *d_out, uint32_t *seq_out, uint32_t *t0, uint32_t *t1, uint32_t *nt_out)
+{
+    for (;;) {
+        if (stop(p.stop))
+            return kExitStop;
+        const unsigned long long v = atom_add(p.cursor, (unsigned long long)want);
+        const uint32_t seq = (uint32_t)(v >> 36);
+        const uint32_t d = (uint32_t)(v >> kTileBits) & 0xffffu;
+        const uint32_t t = (uint32_t)v & kTileMask;
+        if (d < p.nslots) {
+            const uint64_t sn = ld_relaxed_gpu(&p.recs[d].seq_ntiles);
+            const uint32_t nt = (uint32_t)(sn & kTileMask);
+            if ((uint32_t)(sn >> kTileBits) == seq && t < nt) {
+                *d_out = d;
+                *seq_out = seq;
+                *t0 = t;
+                *t1 = t + want < nt ? t + want : nt;
+                *nt_out = nt;
+                last_work = gtime();
+                return 0;
+            }
+        }
+        // The current request has no tiles left: advance, or wait for the
+        // CTA that does.
+        if (atom_cas(p.adv, (unsigned long long)seq, (unsigned long long)((seq + 1) & kSeqMask)) == seq) {
+            const uint32_t r = advance(p, seq, last_work, stop, true);
+            if (r)
+                return r;
+        } else {
+            for (uint32_t spin = 0;; ++spin) {
+                if ((uint32_t)(ld_relaxed_gpu(p.cursor) >> 36) != seq) {
+                    // the server is working even if this CTA's claims keep
+                    // losing: idle means no new request anywhere, so a CTA
+                    // does not exit under light load while others serve
+                    last_work = gtime();
+                    break;
+                }
+                if ((spin & 7) == 7 && (uint32_t)ld_relaxed_gpu(p.adv) == seq)
+                    break;  // the advancer gave up its role: compete for it again
+                if (stop(p.stop))
+                    return kExitStop;
+                if (since(last_work) > (int64_t)p.idle_ns)
+                    return kExitIdle;
+                nap(100);
+            }
+        }
+    }
+}
+
+// ---- per-request claims (claim_mode 1) ----------------------------------
+// No global cursor: every agent walks the dispatched requests in sequence
+// order on its own (`cur`) and claims tiles with atomicAdd on the claim
+// word of the request it stands on.  `low` (the cursor word) is the oldest
+// request that may still have unclaimed tiles; it bounds dispatch (the
+// dispatch ring keeps the entries of requests low .. low + kDispRing - 1)
+// and lets agents that fell behind jump forward.  Several requests are cut
+// into tiles at once, and no agent waits for another to move a cursor.
+
+// a is ahead of b (by less than half the sequence space)
+SRV_INLINE bool seq_after(uint32_t a, uint32_t b)
+{
+    const uint32_t d = (a - b) & kSeqMask;
+    return d != 0 && d < (kSeqMask >> 1);
+}
+
+// Request s has no unclaimed tiles (s must be >= low, so its ring entry is
+// not overwritten yet).  A slot already holding a newer request means s was
+// completed and reaped.
+SRV_FN bool exhausted(const SrvParams &p, uint32_t s)
+{
+    const uint64_t e = ld_relaxed_gpu(p.disp_ring + s % kDispRing);
+    if ((uint32_t)(e >> 36) != s)
+        return false;  // not dispatched yet
+    const uint32_t d = (uint32_t)(e >> kTileBits) & 0xffffu;
+    const uint32_t nt = (uint32_t)e & kTileMask;
+    if (d >= p.nslots)
+        return false;  // a claimer meets it and stops the kernel
+    if (nt == 0)
+        return true;
+    const uint64_t v = ld_relaxed_gpu(&p.recs[d].claim);
+    const uint32_t vs = (uint32_t)(v >> kClaimShift);
+    if (vs == s)
+        return (v & kClaimTileMask) >= nt;
+    return seq_after(vs, s);  // newer: s was reaped; older: s's claim word not seen yet
+}
+
+// The caller found request s without unclaimed tiles: move low from s to
+// s + 1, and on over every following request that is exhausted too.  A
+// failed CAS means low is not s (behind it: whoever moves low to s goes on
+// from there, and waiting agents repeat the check; ahead: nothing to do).
+// The fences order the claim word accesses against the CAS on low (the
+// caller's claim, then its CAS; another agent's CAS, then its look at the
+// claim word), so that one of the two sees the other.
+SRV_FN void help_low(const SrvParams &p, uint32_t s)
+{
+    fence_gpu();
+    for (uint32_t i = 0; i < kDispRing; ++i) {
+        const uint32_t n = (s + 1) & kSeqMask;
+        if (atom_cas(p.cursor, (unsigned long long)s, (unsigned long long)n) != s)
+            return;
+        fence_gpu();
+        s = n;
+        if (!exhausted(p, s))
+            return;
+    }
+}
+
+// Take the dispatch lock at k0 (the value of disp the caller saw) and
+// dispatch up to kDispatchBatch queued requests, no further than the ring
+// allows past low.  Returns the number dispatched.
+SRV_FN uint32_t try_dispatch(const SrvParams &p, uint32_t k0, uint32_t low)
+{
+    const uint32_t used = (k0 - low) & kSeqMask;
+    if (used >= kDispRing)
+        return 0;
+    const uint32_t room = kDispRing - used;
+    const uint32_t n = room < kDispatchBatch ? room : kDispatchBatch;
+    if (atom_cas(p.disp, (unsigned long long)k0, (unsigned long long)k0 | kDispBusy) != k0)
+        return 0;
+    const uint32_t m = dispatch<true>(p, k0, n);
+    atom_exch(p.disp, (unsigned long long)((k0 + m) & kSeqMask));
+    return m;
+}
+
+// Dispatch ahead of an agent standing on request cur while fewer than
+// kLookahead requests are validated ahead of it.
+SRV_FN void lookahead(const SrvParams &p, uint32_t cur)
+{
+    const uint64_t k = ld_relaxed_gpu(p.disp);
+    if (k & kDispBusy)
+        return;
+    if ((((uint32_t)k - cur) & kSeqMask) > kLookahead)
+        return;
+    try_dispatch(p, (uint32_t)k, (uint32_t)ld_relaxed_gpu(p.cursor));
+}
+
+// Claim up to `want` tiles (per-request claims).  Same results as claim().
+SRV_FN uint32_t claim_pr(const SrvParams &p, uint32_t &cur, uint64_t &last_work, StopCheck &stop,
+                             uint32_t want, uint32_t *d_out, uint32_t *seq_out, uint32_t *t0, uint32_t *t1,
+                             uint32_t *nt_out)
+{
+    uint32_t seen_low = (uint32_t)ld_relaxed_gpu(p.cursor);
+    uint32_t backoff = 32;
+    for (;;) {
+        if (stop(p.stop))
+            return kExitStop;
+        const uint32_t low = (uint32_t)ld_relaxed_gpu(p.cursor);
+        if (low != seen_low) {  // the server is making progress
+            seen_low = low;
+            last_work = gtime();
+        }
+        if (seq_after(low, cur))
+            cur = low;
+        const uint64_t e = ld_relaxed_gpu(p.disp_ring + cur % kDispRing);
+        const uint32_t es = (uint32_t)(e >> 36);
+        if (es == cur) {
+            const uint32_t d = (uint32_t)(e >> kTileBits) & 0xffffu;
+            const uint32_t nt = (uint32_t)e & kTileMask;
+            if (d >= p.nslots)
+                return kExitError;  // the host never writes such an entry
+            if (nt) {
+                const uint64_t v = atom_add(&p.recs[d].claim, (unsigned long long)want);
+                const uint32_t vs = (uint32_t)(v >> kClaimShift);
+                const uint64_t t = v & kClaimTileMask;
+                if (vs == cur && t < nt) {
+                    *d_out = d;
+                    *seq_out = cur;
+                    *t0 = (uint32_t)t;
+                    *t1 = t + want < nt ? (uint32_t)t + want : nt;
+                    *nt_out = nt;
+                    last_work = gtime();
+                    if (t + want >= nt) {  // took the request's last tiles
+                        help_low(p, cur);
+                        cur = (cur + 1) & kSeqMask;
+                    }
+                    return 0;
+                }
+                if (vs != cur && !seq_after(vs, cur))
+                    continue;  // cur's claim word not seen yet (it precedes the ring entry): retry
+                if (vs != cur) {
+                    // The slot was reaped and reused: this claim landed on the
+                    // newer request vs, whose record is complete (its claim
+                    // word is set after it); keep the tiles if it has them.
+                    fence_gpu();
+                    const uint64_t sn = ld_relaxed_gpu(&p.recs[d].seq_ntiles);
+                    const uint32_t nt2 = (uint32_t)(sn & kTileMask);
+                    if ((uint32_t)(sn >> kTileBits) == vs && t < nt2) {
+                        *d_out = d;
+                        *seq_out = vs;
+                        *t0 = (uint32_t)t;
+                        *t1 = t + want < nt2 ? (uint32_t)t + want : nt2;
+                        *nt_out = nt2;
+                        last_work = gtime();
+                        return 0;
+                    }
+                }
+            }
+            help_low(p, cur);  // cur has no tiles left
+            cur = (cur + 1) & kSeqMask;
+            backoff = 32;
+            continue;
+        }
+        if (seq_after(es, cur)) {  // the ring moved past cur: it was exhausted long ago
+            cur = (cur + 1) & kSeqMask;
+            continue;
+        }
+        // cur is not dispatched yet: dispatch it if it is next in line
+        const uint64_t k = ld_relaxed_gpu(p.disp);
+        if (k == cur && try_dispatch(p, cur, low)) {
+            last_work = gtime();
+            continue;
+        }
+        if (exhausted(p, low))  // repair: low stopped on a request that is exhausted
+            help_low(p, low);
+        if (since(last_work) > (int64_t)p.idle_ns)
+            return kExitIdle;
+        nap(backoff);
+        backoff = backoff < 256 ? 2 * backoff : 256;
+    }
+}
+
+
+// ---- the agent's steps (one per resident CTA) ------------------------------
+
+// Claim up to `want` tiles for the agent's workers, by either protocol.
+// adv_after: (global cursor) this claim took its request's last tiles, so
+// the cursor is moved on once they are queued (lease_queued).
+template <bool PER_REQ>
+SRV_INLINE uint32_t agent_claim(const SrvParams &p, uint32_t &cur, uint64_t &last_work, StopCheck &stop,
+                                uint32_t want, uint32_t *d, uint32_t *seq, uint32_t *t0, uint32_t *t1,
+                                bool &adv_after)
+{
+    uint32_t nt = 0;
+    const uint32_t code = PER_REQ ? claim_pr(p, cur, last_work, stop, want, d, seq, t0, t1, &nt)
+                                  : claim(p, last_work, stop, want, d, seq, t0, t1, &nt);
+    adv_after = !PER_REQ && code == 0 && *t1 == nt;
+    return code;
+}
+
+// The tiles of the agent's last claim (of request lseq) are queued for its
+// workers.  Per-request claims: validate requests ahead.  Global cursor: if
+// the claim took the request's last tiles, move the cursor on now instead of
+// waiting for a claim to fail (without waiting, if the next request is not
+// ready).  Returns 0 or an exit code.
+template <bool PER_REQ>
+SRV_INLINE uint32_t lease_queued(const SrvParams &p, uint32_t cur, uint32_t lseq, bool &adv_after,
+                                 uint64_t &last_work, StopCheck &stop)
+{
+    if (PER_REQ) {
+        lookahead(p, cur);
+        return 0;
+    }
+    if (!adv_after)
+        return 0;
+    adv_after = false;
+    if (atom_cas(p.adv, (unsigned long long)lseq, (unsigned long long)((lseq + 1) & kSeqMask)) == lseq) {
+        const uint32_t r = advance(p, lseq, last_work, stop, false);
+        if (r && r != kNotReady)
+            return r;
+    }
+    return 0;
+}
+
+// A worker finished one tile of the request in slot d; the worker finishing
+// the last one raises the request's completion word in host memory
+// (system-scope release after a system-scope fence over its output stores).
+SRV_INLINE void tile_finished(const SrvParams &p, uint32_t d)
+{
+    SrvRec *rec = p.recs + d;
+    const uint32_t ntiles = (uint32_t)(ld_relaxed_gpu(&rec->seq_ntiles) & kTileMask);
+    const unsigned int prev = atom_add(&rec->done_tiles, 1u);
+    if (prev + 1 == ntiles) {
+        fence_sys();
+        st_release_sys(p.done + d, (ld_cg(&rec->gen) << 2) | 1u);
+    }
+}
+
+}  // namespace srvp

@@ -49,6 +49,7 @@
 #include "common.cuh"
 #include "aes_ttable.cuh"
 #include "tile.cuh"
+#include "served_protocol.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -62,367 +63,7 @@
 
 namespace {
 
-constexpr uint32_t kSeqMask = (1u << 28) - 1;
-constexpr uint32_t kTileBits = 20;
-constexpr uint32_t kTileMask = (1u << kTileBits) - 1;
-constexpr uint32_t kMaxTiles = (1u << kTileBits) - 16384;  // headroom for batched exhausted claims
-constexpr int kMaxSlots = 65535;
-constexpr uint32_t kExitStop = 1, kExitIdle = 2, kExitError = 4;
-constexpr uint32_t kNotReady = 8;  // advance(): next request not ready (not an exit reason)
-constexpr uint32_t kFlagHostOut = 1;   // QEntry.flags: the output is pinned host memory
-constexpr uint32_t kFlagEmulated = 2;  // QEntry.flags: emulated offload, len = duration in ns
-constexpr uint64_t kMaxEmulatedNs = 10000000;
-constexpr int kMaxWarps = 16;   // CTA of at most 512 threads (128 registers each: round keys in registers)
-constexpr uint32_t kRing = 64;  // >= workers + prefetch
-// Tiles an agent keeps queued for its workers.  A deep queue rides through
-// the microseconds the global cursor needs to move from one request to the
-// next (8 MiB AES-256 stream: 440 GB/s with 1 queued tile, 664 with 16).
-constexpr uint32_t kPrefetch = 16;
-constexpr uint32_t kMaxClaim = 4;    // tiles per claim: spreads a request over many SMs
-constexpr uint32_t kLookahead = 8;   // requests validated ahead of the cursor
-constexpr uint32_t kDispRing = 64;   // > kLookahead
-constexpr uint32_t kDispatchBatch = 4;  // queue entries read per round trip over the host link
-
-struct QEntry {  // 64 bytes, host-written, tag last
-    uint64_t tag;  // sequence number + 1
-    uint64_t in, out, len, iv_hi, iv_lo, gen;
-    uint32_t key_slot;
-    uint16_t desc;   // slot index d
-    uint16_t flags;  // kFlagHostOut, kFlagEmulated
-};
-static_assert(sizeof(QEntry) == 64, "QEntry layout");
-
-struct SrvRec {  // device-only, 128 bytes
-    aesrt::BatchReq rq;             // rq.pad holds the flags
-    unsigned long long seq_ntiles;  // (seq << 20) | ntiles, written after the rest
-    unsigned long long gen;
-    unsigned int tile_groups;       // this request's tile: tile_groups groups, or
-    unsigned int tile_parts;        // 1/tile_parts of one group
-    unsigned int done_tiles;
-    unsigned int pad[9];
-};
-static_assert(offsetof(SrvRec, tile_groups) % 8 == 0, "tile shape words are 8-byte aligned");
-static_assert(sizeof(SrvRec) == 128, "SrvRec layout");
-
-struct SrvParams {
-    unsigned long long *cursor;
-    unsigned long long *adv;
-    unsigned long long *disp;      // next sequence number to dispatch (validate into recs)
-    unsigned long long *disp_ring; // kDispRing: ring_entry() of dispatched request s at s % kDispRing
-    SrvRec *recs;
-    const uint4 *keys;          // max_keys x 15 round keys
-    const int *key_nr;          // max_keys; 0 = unregistered
-    const QEntry *queue;        // mapped
-    unsigned long long *done;   // mapped
-    const unsigned int *stop;   // mapped
-    unsigned int *kstatus;      // mapped
-    const uint32_t *te0;
-    uint32_t qmask, max_keys, tile_blocks, nslots;  // tile_blocks 0 = chosen per request
-    uint64_t idle_ns, max_len;
-};
-
-__device__ __forceinline__ uint64_t gtime()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Nanoseconds since t0, as a signed count: a timer that steps back reads as
-// negative (not idle) instead of wrapping to a huge unsigned difference.
-__device__ __forceinline__ int64_t since(uint64_t t0)
-{
-    return (int64_t)(gtime() - t0);
-}
-__device__ __forceinline__ void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
-{
-    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
-}
-__device__ __forceinline__ uint64_t ld_relaxed_gpu(const unsigned long long *p)
-{
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_gpu(unsigned long long *p, uint64_t v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_release_sys(unsigned long long *p, uint64_t v)
-{
-    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t ld_volatile(const unsigned int *p)
-{
-    return *reinterpret_cast<const volatile unsigned int *>(p);
-}
-
-// The stop flag lives in host memory (one NVLink-C2C round trip per read),
-// so spinning loops look at it at most every 50 us.
-struct StopCheck {
-    uint64_t next = 0;
-    __device__ __forceinline__ bool operator()(const unsigned int *flag)
-    {
-        const uint64_t now = gtime();
-        const int64_t ahead = (int64_t)(next - now);
-        if (ahead > 0 && ahead <= 50000)  // read within the last 50 us (and the timer did not step back)
-            return false;
-        next = now + 50000;
-        return ld_volatile(flag) != 0;
-    }
-};
-
-// Entry of the dispatch ring for request k: sequence number (28 bits), slot
-// d (16 bits; 0xffff marks a queue entry the host never writes) and tile
-// count (20 bits).  It is stored after the request's record is complete, so
-// an entry that carries k is all the advancer needs to move the cursor.
-__device__ __forceinline__ uint64_t ring_entry(uint32_t k, uint32_t d, uint32_t ntiles)
-{
-    return ((uint64_t)k << 36) | ((uint64_t)d << kTileBits) | ntiles;
-}
-
-__device__ __forceinline__ uint64_t ld_relaxed_sys(const uint64_t *p)
-{
-    uint64_t v;
-    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Dispatch, in sequence order, up to n_max requests starting at k0 (the
-// value of disp the caller saw) whose queue entries are present: their tags
-// are read in one round trip over the host link and the requests claimed
-// with one CAS on disp (one dispatcher per request); then the entries are
-// read (acquire pattern: relaxed tag loads, then a system-scope fence) and
-// validated into recs[d], and finally their dispatch-ring entries are
-// published.  A request without tiles is completed here.  Returns the number
-// of requests dispatched (0: k0 not queued yet, or someone else took it) and,
-// in *first, the ring entry of request k0.
-__device__ __noinline__ uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, uint64_t *first = nullptr)
-{
-    uint32_t m = 0;
-    {
-        uint64_t tag[kDispatchBatch];
-#pragma unroll
-        for (uint32_t i = 0; i < kDispatchBatch; ++i)
-            tag[i] = i < n_max ? ld_relaxed_sys(&p.queue[(k0 + i) & p.qmask].tag) : 0;
-#pragma unroll
-        for (uint32_t i = 0; i < kDispatchBatch; ++i)
-            if (m == i && i < n_max && (uint32_t)(tag[i] & kSeqMask) == ((k0 + i + 1) & kSeqMask))
-                m = i + 1;
-    }
-    if (m == 0)
-        return 0;
-    asm volatile("fence.acq_rel.sys;" ::: "memory");
-    if (atomicCAS(p.disp, (unsigned long long)k0, (unsigned long long)((k0 + m) & kSeqMask)) != k0)
-        return 0;
-    uint64_t x[kDispatchBatch][7];
-#pragma unroll
-    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
-        if (i < m) {
-            const uint64_t *e = reinterpret_cast<const uint64_t *>(p.queue + ((k0 + i) & p.qmask));
-            uint64_t unused;
-            ld_volatile_v2(e + 0, unused, x[i][0]);
-            ld_volatile_v2(e + 2, x[i][1], x[i][2]);
-            ld_volatile_v2(e + 4, x[i][3], x[i][4]);
-            ld_volatile_v2(e + 6, x[i][5], x[i][6]);
-            (void)unused;
-        }
-    }
-    uint64_t ent[kDispatchBatch] = {};
-    uint32_t done_word[kDispatchBatch] = {};  // status for a request completed here, else 0
-#pragma unroll
-    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
-        if (i >= m)
-            continue;
-        const uint32_t k = (k0 + i) & kSeqMask;
-        const uint64_t in = x[i][0], out = x[i][1], len = x[i][2], iv_hi = x[i][3], iv_lo = x[i][4];
-        const uint32_t ks = (uint32_t)x[i][6];
-        const uint32_t d = (uint32_t)(x[i][6] >> 32) & 0xffffu;
-        const uint32_t flags = (uint32_t)(x[i][6] >> 48);
-        done_word[i] = 0;
-        if (d >= p.nslots) {  // the host never writes such an entry; the advancer stops on it
-            ent[i] = ring_entry(k, 0xffffu, 0);
-            continue;
-        }
-        int nr = 0;
-        if (ks < p.max_keys)
-            nr = __ldcg(p.key_nr + ks);
-        bool ok = (nr == 10 || nr == 12 || nr == 14) && len <= p.max_len;
-        if (ok && len)
-            ok = in && out && !((in | out) & 15u);
-        uint32_t ntiles = 0, tg = 1, tp = 1;
-        const bool emulated = (flags & kFlagEmulated) != 0;
-        if (emulated) {  // one tile that holds a worker warp for len ns; no key, no payload
-            ok = len <= kMaxEmulatedNs;
-            ntiles = ok ? 1u : 0u;
-            nr = 0;
-        } else if (ok && len) {
-            // tiles are runs of tg whole 256-block counter groups, or (tp > 1)
-            // equal parts of one group.  Unless fixed by the server config, a
-            // request is cut into about 512 tiles of 64..1024 blocks: short
-            // requests spread over many warps, long ones keep claims rare.
-            const uint64_t nb = (len + 15) >> 4;
-            const uint64_t groups = (((iv_lo & 255u) + nb - 1) >> 8) + 1;
-            uint32_t tb = p.tile_blocks;
-            if (!tb) {
-                tb = 64;
-                while (tb < 1024 && (uint64_t)tb * 512 < nb)
-                    tb <<= 1;
-            }
-            if (tb >= 256)
-                tg = tb / 256;
-            else
-                tp = 256 / tb;
-            ntiles = (uint32_t)((groups + tg - 1) / tg * tp);
-        }
-        SrvRec *rec = p.recs + d;
-        rec->rq.in = reinterpret_cast<const uint4 *>(in);
-        rec->rq.out = reinterpret_cast<uint4 *>(out);
-        rec->rq.len = len;
-        rec->rq.iv_hi = iv_hi;
-        rec->rq.iv_lo = iv_lo;
-        rec->rq.rk = p.keys + 15u * (ok && !emulated ? ks : 0u);
-        rec->rq.nr = (uint32_t)nr;
-        rec->rq.pad = flags;
-        rec->gen = x[i][5];
-        rec->done_tiles = 0;
-        rec->tile_groups = tg;
-        rec->tile_parts = tp;
-        ent[i] = ring_entry(k, d, ntiles);
-        if (ntiles == 0)
-            done_word[i] = ok ? 1u : 2u;
-    }
-    __threadfence();
-#pragma unroll
-    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
-        const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
-        if (i < m && d != 0xffffu)
-            st_relaxed_gpu(&p.recs[d].seq_ntiles, ((ent[i] >> 36) << kTileBits) | (ent[i] & kTileMask));
-    }
-    __threadfence();
-#pragma unroll
-    for (uint32_t i = 0; i < kDispatchBatch; ++i)
-        if (i < m)
-            st_relaxed_gpu(p.disp_ring + ((k0 + i) % kDispRing), ent[i]);
-#pragma unroll
-    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
-        if (i < m && done_word[i]) {
-            const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
-            __threadfence_system();
-            st_release_sys(p.done + d, (x[i][5] << 2) | done_word[i]);
-        }
-    }
-    if (first)
-        *first = ent[0];
-    return m;
-}
-
-// Elected advancer (adv has been moved from seq to seq + 1): move the cursor
-// to request seq + 1 once its dispatch-ring entry is published (dispatching
-// it, with what is queued behind it, if it is next in line), step over
-// requests without tiles, and dispatch up to kLookahead requests ahead.
-// With block == false the role is handed back at once (kNotReady) when the
-// next request is not ready.  Returns 0, kNotReady or an exit code (after
-// handing the role back).
-__device__ __noinline__ uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_work, StopCheck &stop,
-                                        bool block)
-{
-    for (;;) {
-        const uint32_t nseq = (seq + 1) & kSeqMask;
-        uint64_t e = 0;
-        for (;;) {
-            e = ld_relaxed_gpu(p.disp_ring + (nseq % kDispRing));
-            if ((uint32_t)(e >> 36) == nseq)
-                break;  // dispatched and published
-            const uint32_t dsp = (uint32_t)ld_relaxed_gpu(p.disp);
-            if (dsp == nseq && dispatch(p, nseq, kLookahead + 1, &e))
-                break;  // dispatched it here: e is its ring entry
-            uint32_t r = 0;
-            if (!block)
-                r = kNotReady;
-            else if (stop(p.stop))
-                r = kExitStop;
-            else if (since(last_work) > (int64_t)p.idle_ns)
-                r = kExitIdle;
-            if (r) {
-                atomicCAS(p.adv, (unsigned long long)nseq, (unsigned long long)seq);
-                return r;
-            }
-            __nanosleep(32);
-        }
-        const uint32_t d = (uint32_t)(e >> kTileBits) & 0xffffu;
-        if (d >= p.nslots)
-            return kExitError;
-        // Only the elected advancer changes the sequence number; claims that
-        // raced with it only added to the tile count of the old request.
-        atomicExch(p.cursor, ((unsigned long long)nseq << 36) | ((unsigned long long)d << kTileBits));
-        last_work = gtime();
-        const uint32_t k = (uint32_t)ld_relaxed_gpu(p.disp);
-        const uint32_t ahead = (k - nseq) & kSeqMask;
-        if (ahead <= kLookahead)
-            dispatch(p, k, kLookahead + 1 - ahead);
-        if (e & kTileMask)
-            return 0;
-        // nothing to claim in nseq: step over it, unless another agent
-        // (which saw the empty request) already took that role
-        if (atomicCAS(p.adv, (unsigned long long)nseq, (unsigned long long)((nseq + 1) & kSeqMask)) != nseq)
-            return 0;
-        seq = nseq;
-    }
-}
-
-// Claim up to `want` tiles of the current request (the agent of a CTA).
-// Returns 0 with the tiles [*t0, *t1) of slot *d and its sequence number, or
-// an exit code.
-__device__ uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &stop, uint32_t want,
-                          uint32_t *d_out, uint32_t *seq_out, uint32_t *t0, uint32_t *t1, uint32_t *nt_out)
-{
-    for (;;) {
-        if (stop(p.stop))
-            return kExitStop;
-        const unsigned long long v = atomicAdd(p.cursor, (unsigned long long)want);
-        const uint32_t seq = (uint32_t)(v >> 36);
-        const uint32_t d = (uint32_t)(v >> kTileBits) & 0xffffu;
-        const uint32_t t = (uint32_t)v & kTileMask;
-        if (d < p.nslots) {
-            const uint64_t sn = ld_relaxed_gpu(&p.recs[d].seq_ntiles);
-            const uint32_t nt = (uint32_t)(sn & kTileMask);
-            if ((uint32_t)(sn >> kTileBits) == seq && t < nt) {
-                *d_out = d;
-                *seq_out = seq;
-                *t0 = t;
-                *t1 = t + want < nt ? t + want : nt;
-                *nt_out = nt;
-                last_work = gtime();
-                return 0;
-            }
-        }
-        // The current request has no tiles left: advance, or wait for the
-        // CTA that does.
-        if (atomicCAS(p.adv, (unsigned long long)seq, (unsigned long long)((seq + 1) & kSeqMask)) == seq) {
-            const uint32_t r = advance(p, seq, last_work, stop, true);
-            if (r)
-                return r;
-        } else {
-            for (uint32_t spin = 0;; ++spin) {
-                if ((uint32_t)(ld_relaxed_gpu(p.cursor) >> 36) != seq) {
-                    // the server is working even if this CTA's claims keep
-                    // losing: idle means no new request anywhere, so a CTA
-                    // does not exit under light load while others serve
-                    last_work = gtime();
-                    break;
-                }
-                if ((spin & 7) == 7 && (uint32_t)ld_relaxed_gpu(p.adv) == seq)
-                    break;  // the advancer gave up its role: compete for it again
-                if (stop(p.stop))
-                    return kExitStop;
-                if (since(last_work) > (int64_t)p.idle_ns)
-                    return kExitIdle;
-                __nanosleep(100);
-            }
-        }
-    }
-}
+using namespace srvp;
 
 // Round keys in registers, read through L2 (coherent): the resident kernel
 // outlives key registrations, and adjacent 240-byte key slots share cache
@@ -462,10 +103,13 @@ struct Ring {
 };
 
 // Agent warp, lane 0: keep the ring kPrefetch items ahead of the workers.
+// PER_REQ selects per-request claims (claim_mode 1) over the global cursor.
+template <bool PER_REQ>
 __device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
 {
     uint64_t last_work = gtime();
     StopCheck stop;
+    uint32_t cur = PER_REQ ? (uint32_t)ld_relaxed_gpu(p.cursor) : 0u;  // request this agent stands on
     uint32_t ld = 0, lseq = 0, lt = 0, lend = 0;  // current lease: tiles [lt, lend) of slot ld
     bool adv_after = false;                      // the lease ends its request
     uint32_t code = 0;
@@ -488,11 +132,9 @@ __device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
         if (lt >= lend) {
             const uint32_t waiting = (int32_t)(head - tail) > 0 ? head - tail : 0u;
             const uint32_t want = waiting + kPrefetch < kMaxClaim ? waiting + kPrefetch : kMaxClaim;
-            uint32_t nt = 0;
-            code = claim(p, last_work, stop, want, &ld, &lseq, &lt, &lend, &nt);
+            code = agent_claim<PER_REQ>(p, cur, last_work, stop, want, &ld, &lseq, &lt, &lend, adv_after);
             if (code)
                 break;
-            adv_after = lend == nt;  // this claim took the request's last tiles
         }
         const uint32_t slot = tail % kRing;
         ring.d[slot] = ld;
@@ -502,24 +144,17 @@ __device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
         backoff = 32;
         __threadfence_block();
         ring.tail = tail + 1;
-        if (adv_after && lt >= lend) {
-            // All of this request's tiles are claimed and ours are queued:
-            // move the cursor on now instead of waiting for a claim to fail
-            // (without waiting, if the next request is not ready).
-            adv_after = false;
-            if (atomicCAS(p.adv, (unsigned long long)lseq, (unsigned long long)((lseq + 1) & kSeqMask)) == lseq) {
-                const uint32_t r = advance(p, lseq, last_work, stop, false);
-                if (r && r != kNotReady) {
-                    code = r;
-                    break;
-                }
-            }
+        if (lt >= lend) {  // the whole lease is queued
+            code = lease_queued<PER_REQ>(p, cur, lseq, adv_after, last_work, stop);
+            if (code)
+                break;
         }
     }
     __threadfence_block();
     ring.exit_code = code;
 }
 
+template <bool PER_REQ>
 __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ SrvParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -536,7 +171,7 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     if (warp == 0) {
         if (lane == 0) {
-            agent(p, ring);
+            agent<PER_REQ>(p, ring);
             if (ring.exit_code)
                 atomicOr_system(p.kstatus, ring.exit_code);
         }
@@ -618,14 +253,8 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
         else
             __threadfence();
         __syncwarp();
-        if (lane == 0) {
-            const uint32_t ntiles = (uint32_t)(ld_relaxed_gpu(&rec->seq_ntiles) & kTileMask);
-            const unsigned int prev = atomicAdd(&rec->done_tiles, 1u);
-            if (prev + 1 == ntiles) {
-                __threadfence_system();
-                st_release_sys(p.done + d, (__ldcg(&rec->gen) << 2) | 1u);
-            }
-        }
+        if (lane == 0)
+            tile_finished(p, d);
     }
 }
 
@@ -636,6 +265,7 @@ using namespace aesrt;
 struct offload_server_s {
     int device = -1;
     int slots = 0, max_keys = 0, ctas = 0, threads = 0, tile_blocks = 0;
+    int claim_mode = 0;  // 0: global cursor, 1: per-request claims
     uint32_t qsize = 0;
     uint64_t budget = 0, max_len = 0, idle_ns = 0;
     // mapped host memory
@@ -669,7 +299,10 @@ namespace {
 int launch_resident(offload_server_s *s)
 {
     s->ctrl[1] = 0;
-    server_kernel<<<s->ctas, s->threads, aestt::kTableBytes, s->stream>>>(s->params);
+    if (s->claim_mode)
+        server_kernel<true><<<s->ctas, s->threads, aestt::kTableBytes, s->stream>>>(s->params);
+    else
+        server_kernel<false><<<s->ctas, s->threads, aestt::kTableBytes, s->stream>>>(s->params);
     cudaError_t e = cudaGetLastError();
     if (e)
         return cuda_fail(e, "server_kernel launch");
@@ -793,7 +426,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
         ctas > st->nsm || threads < 64 || threads > 32 * kMaxWarps || (threads & 31) ||
         !(tile_blocks == 0 || tile_blocks == 64 || tile_blocks == 128 ||
           (tile_blocks >= 256 && tile_blocks % 256 == 0)) ||
-        tile_blocks > (1 << 22))
+        tile_blocks > (1 << 22) || c.claim_mode < 0 || c.claim_mode > 1)
         return AES_EINVAL;
     offload_server_s *s = new (std::nothrow) offload_server_s();
     if (!s)
@@ -804,6 +437,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     s->ctas = ctas;
     s->threads = threads;
     s->tile_blocks = tile_blocks;
+    s->claim_mode = c.claim_mode;
     s->budget = c.hbm_budget;
     s->idle_ns = 1000ull * (c.idle_timeout_us ? c.idle_timeout_us : 200000u);
     // tiles of at least 64 blocks (1024 adaptive for long requests) keep the tile count < kMaxTiles
@@ -865,8 +499,11 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     if ((e = cudaStreamCreateWithFlags(&s->setup, cudaStreamNonBlocking)))
         return fail("cudaStreamCreate");
     const unsigned long long first_seq = 1;  // request sequence numbers start at 1
+    // per-request claims: the cursor word is low, the oldest request that
+    // may have unclaimed tiles, and starts at the first sequence number
     if ((e = cudaMemsetAsync(s->dmem, 0, dbytes, s->setup)) ||
         (e = cudaMemcpyAsync(s->dmem + off_disp, &first_seq, 8, cudaMemcpyHostToDevice, s->setup)) ||
+        (s->claim_mode && (e = cudaMemcpyAsync(s->dmem, &first_seq, 8, cudaMemcpyHostToDevice, s->setup))) ||
         (e = cudaStreamSynchronize(s->setup)))
         return fail("cudaMemset(server)");
     SrvParams &P = s->params;
@@ -896,7 +533,9 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     P.nslots = (uint32_t)slots;
     P.idle_ns = s->idle_ns;
     P.max_len = s->max_len;
-    if ((e = cudaFuncSetAttribute(server_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(server_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)aestt::kTableBytes)) ||
+        (e = cudaFuncSetAttribute(server_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)aestt::kTableBytes)))
         return fail("cudaFuncSetAttribute(server)");
     rc = launch_resident(s);

@@ -1,0 +1,410 @@
+// served_protocol_sim.cpp -- host threads stand in for the served kernel's
+// resident CTAs and run its request protocol (served_protocol.cuh, compiled
+// for the host) against a producer that submits and reaps requests the way
+// offload_submit / offload_poll do.  Each CTA is an agent thread (claims
+// tiles, queues them) and a worker thread (takes queued tiles, finishes
+// them).  Checked: every tile of every request is processed exactly once
+// and while its request still owns the slot, every request completes once
+// with the right status, zero-length and rejected requests complete at
+// dispatch, and idle exits, relaunches and the stop flag behave.  Logic
+// only: host memory ordering is not the GPU's.
+//
+// usage: served_protocol_sim mode ctas slots requests tile_blocks idle_us seed
+#include "served_protocol.cuh"
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <random>
+#include <thread>
+#include <vector>
+
+using namespace srvp;
+
+namespace {
+
+constexpr int kMaxKeys = 4;
+constexpr uint32_t kQueueCap = 16;  // tiles an agent keeps queued
+
+struct alignas(64) Word {
+    unsigned long long v = 0;
+};
+
+struct Req {
+    uint64_t len = 0;
+    uint64_t iv_lo = 0;
+    int key_slot = 0;
+    bool valid = true;
+    uint32_t ntiles = 0;                       // expected tile count
+    std::unique_ptr<std::atomic<uint8_t>[]> marks;
+    std::atomic<int> completions{0};
+};
+
+struct Tile {
+    uint32_t d, t, seq;
+};
+
+// One stand-in CTA: agent + worker sharing a small queue.
+struct Cta {
+    std::mutex mu;
+    std::vector<Tile> q;
+    std::atomic<bool> agent_done{false};
+    std::atomic<uint32_t> exit_code{0};
+};
+
+struct Sim {
+    int mode = 0, nctas = 4, slots = 64, nreq = 2000, tile_blocks = 0;
+    uint64_t idle_ns = 2000000;
+    uint32_t seed = 1;
+
+    Word cursor, adv, disp;
+    std::vector<unsigned long long> ring;
+    SrvRec *recs = nullptr;
+    std::vector<uint4> keys;
+    std::vector<int> key_nr;
+    QEntry *queue = nullptr;
+    uint32_t qsize = 1;
+    std::vector<unsigned long long> done;
+    unsigned int ctrl[16] = {};
+    SrvParams P{};
+
+    std::unique_ptr<Req[]> reqs;
+    std::atomic<int> errors{0};
+    std::mutex err_mu;
+    char first_error[256] = "";
+    std::atomic<uint64_t> tiles_done{0};
+
+    std::vector<std::thread> threads;
+    std::vector<std::unique_ptr<Cta>> ctas;
+    std::atomic<int> live{0};
+    int launches = 0;
+
+    void fail(const char *fmt, uint64_t a = 0, uint64_t b = 0, uint64_t c = 0)
+    {
+        std::lock_guard<std::mutex> lk(err_mu);
+        if (errors.fetch_add(1) == 0)
+            std::snprintf(first_error, sizeof(first_error), fmt, (unsigned long long)a, (unsigned long long)b,
+                          (unsigned long long)c);
+    }
+
+    void setup()
+    {
+        ring.assign(kDispRing, 0);
+        recs = static_cast<SrvRec *>(std::aligned_alloc(128, sizeof(SrvRec) * (size_t)slots));
+        std::memset(recs, 0, sizeof(SrvRec) * (size_t)slots);
+        keys.assign(15 * kMaxKeys, make_uint4(0, 0, 0, 0));
+        key_nr.assign(kMaxKeys, 0);
+        key_nr[0] = 10;
+        key_nr[1] = 14;
+        key_nr[2] = 12;  // key slot 3 stays unregistered: requests naming it are rejected
+        while (qsize < (uint32_t)slots)
+            qsize <<= 1;
+        queue = static_cast<QEntry *>(std::aligned_alloc(64, sizeof(QEntry) * qsize));
+        std::memset(queue, 0, sizeof(QEntry) * qsize);
+        done.assign((size_t)slots, 0);
+        disp.v = 1;                 // sequence numbers start at 1
+        cursor.v = mode ? 1 : 0;    // per-request claims: low starts at the first sequence number
+        P.cursor = &cursor.v;
+        P.adv = &adv.v;
+        P.disp = &disp.v;
+        P.disp_ring = ring.data();
+        P.recs = recs;
+        P.keys = keys.data();
+        P.key_nr = key_nr.data();
+        P.queue = queue;
+        P.done = done.data();
+        P.stop = &ctrl[0];
+        P.kstatus = &ctrl[1];
+        P.te0 = nullptr;
+        P.qmask = qsize - 1;
+        P.max_keys = kMaxKeys;
+        P.tile_blocks = (uint32_t)tile_blocks;
+        P.nslots = (uint32_t)slots;
+        P.idle_ns = idle_ns;
+        P.max_len = 1ull << 40;
+    }
+
+    // The tile count dispatch gives a request (restated here to size the
+    // per-tile marks and to check the record against).
+    uint32_t tile_count(uint64_t len, uint64_t iv_lo) const
+    {
+        if (len == 0)
+            return 0;
+        const uint64_t nb = (len + 15) >> 4;
+        const uint64_t groups = (((iv_lo & 255u) + nb - 1) >> 8) + 1;
+        uint32_t tb = (uint32_t)tile_blocks;
+        if (!tb) {
+            tb = 64;
+            while (tb < 1024 && (uint64_t)tb * 512 < nb)
+                tb <<= 1;
+        }
+        const uint32_t tg = tb >= 256 ? tb / 256 : 1, tp = tb >= 256 ? 1 : 256 / tb;
+        return (uint32_t)((groups + tg - 1) / tg * tp);
+    }
+
+    template <bool PER_REQ>
+    void agent(Cta *c)
+    {
+        uint64_t last_work = gtime();
+        StopCheck stop;
+        uint32_t cur = PER_REQ ? (uint32_t)ld_relaxed_gpu(P.cursor) : 0u;
+        bool adv_after = false;
+        uint32_t code = 0;
+        for (;;) {
+            bool full;
+            {
+                std::lock_guard<std::mutex> lk(c->mu);
+                full = c->q.size() >= kQueueCap;
+            }
+            if (full) {  // let the worker catch up
+                if (stop(P.stop)) {
+                    code = kExitStop;
+                    break;
+                }
+                std::this_thread::yield();
+                continue;
+            }
+            uint32_t d = 0, seq = 0, t0 = 0, t1 = 0;
+            code = agent_claim<PER_REQ>(P, cur, last_work, stop, kMaxClaim, &d, &seq, &t0, &t1, adv_after);
+            if (code)
+                break;
+            if (t1 <= t0 || t1 - t0 > kMaxClaim)
+                fail("claim of %llu..%llu tiles of seq %llu", t0, t1, seq);
+            {
+                std::lock_guard<std::mutex> lk(c->mu);
+                for (uint32_t t = t0; t < t1; ++t)
+                    c->q.push_back(Tile{d, t, seq});
+            }
+            code = lease_queued<PER_REQ>(P, cur, seq, adv_after, last_work, stop);
+            if (code)
+                break;
+        }
+        c->exit_code.store(code);
+        if (code & kExitError)
+            fail("agent stopped with ERROR");
+        __atomic_fetch_or(P.kstatus, code, __ATOMIC_RELAXED);
+        c->agent_done.store(true);
+    }
+
+    void worker(Cta *c)
+    {
+        for (;;) {
+            Tile tl{};
+            bool have = false;
+            {
+                std::lock_guard<std::mutex> lk(c->mu);
+                if (!c->q.empty()) {
+                    tl = c->q.front();
+                    c->q.erase(c->q.begin());
+                    have = true;
+                }
+            }
+            if (!have) {
+                if (c->agent_done.load()) {
+                    std::lock_guard<std::mutex> lk(c->mu);
+                    if (c->q.empty())
+                        break;
+                    continue;
+                }
+                std::this_thread::yield();
+                continue;
+            }
+            process(tl);
+            tile_finished(P, tl.d);
+        }
+        live.fetch_sub(1);
+    }
+
+    void process(const Tile &tl)
+    {
+        const uint64_t sn = ld_relaxed_gpu(&recs[tl.d].seq_ntiles);
+        const uint32_t nt = (uint32_t)(sn & kTileMask);
+        if ((uint32_t)(sn >> kTileBits) != tl.seq || tl.t >= nt) {
+            fail("tile %llu of seq %llu: slot holds seq %llu", tl.t, tl.seq, sn >> kTileBits);
+            return;
+        }
+        const uint64_t idx = tl.seq - 1;
+        if (idx >= (uint64_t)nreq) {
+            fail("tile of unknown seq %llu", tl.seq);
+            return;
+        }
+        Req &r = reqs[idx];
+        if (nt != r.ntiles) {
+            fail("seq %llu: record has %llu tiles, expected %llu", tl.seq, nt, r.ntiles);
+            return;
+        }
+        if (r.marks[tl.t].exchange(1) != 0)
+            fail("tile %llu of seq %llu processed twice", tl.t, tl.seq);
+        tiles_done.fetch_add(1);
+    }
+
+    void launch()
+    {
+        for (auto &t : threads)
+            t.join();
+        threads.clear();
+        ctas.clear();
+        ctrl[1] = 0;
+        ++launches;
+        live.store(nctas);
+        for (int i = 0; i < nctas; ++i) {
+            ctas.emplace_back(new Cta());
+            Cta *c = ctas.back().get();
+            if (mode)
+                threads.emplace_back([this, c] { agent<true>(c); });
+            else
+                threads.emplace_back([this, c] { agent<false>(c); });
+            threads.emplace_back([this, c] { worker(c); });
+        }
+    }
+
+    // offload_submit's relaunch rule: start the CTAs again once all of them
+    // have exited.
+    void ensure_running()
+    {
+        if (live.load() == 0)
+            launch();
+    }
+
+    int run()
+    {
+        setup();
+        std::mt19937_64 g(seed);
+        reqs.reset(new Req[(size_t)nreq]);
+        for (int i = 0; i < nreq; ++i) {
+            Req &r = reqs[(size_t)i];
+            const int kind = (int)(g() % 20);
+            if (kind == 0)
+                r.len = 0;
+            else if (kind < 12)
+                r.len = 1 + g() % 8192;
+            else if (kind < 18)
+                r.len = 1 + g() % (256u << 10);
+            else
+                r.len = 1 + g() % (2u << 20);
+            r.iv_lo = g();
+            r.key_slot = (int)(g() % kMaxKeys);
+            r.valid = key_nr[(size_t)r.key_slot] != 0;
+            r.ntiles = r.valid ? tile_count(r.len, r.iv_lo) : 0;
+            r.marks.reset(new std::atomic<uint8_t>[r.ntiles ? r.ntiles : 1]);
+            for (uint32_t t = 0; t < r.ntiles; ++t)
+                r.marks[t].store(0);
+        }
+        std::vector<uint32_t> free_slots;
+        for (int i = slots - 1; i >= 0; --i)
+            free_slots.push_back((uint32_t)i);
+        std::vector<uint64_t> gen((size_t)slots, 0);
+        std::vector<int64_t> owner((size_t)slots, -1);
+        int inflight = 0, completed = 0;
+        auto reap = [&]() {
+            for (int d = 0; d < slots; ++d) {
+                if (owner[(size_t)d] < 0)
+                    continue;
+                const uint64_t v = __atomic_load_n(&done[(size_t)d], __ATOMIC_ACQUIRE);
+                if ((v >> 2) != gen[(size_t)d])
+                    continue;
+                Req &r = reqs[(size_t)owner[(size_t)d]];
+                const uint32_t status = (uint32_t)(v & 3);
+                if (status != (r.valid ? 1u : 2u))
+                    fail("seq %llu completed with status %llu", (uint64_t)owner[(size_t)d] + 1, status);
+                for (uint32_t t = 0; t < r.ntiles; ++t)
+                    if (r.marks[t].load() != 1)
+                        fail("seq %llu completed with tile %llu unprocessed", (uint64_t)owner[(size_t)d] + 1, t);
+                r.completions.fetch_add(1);
+                owner[(size_t)d] = -1;
+                free_slots.push_back((uint32_t)d);
+                --inflight;
+                ++completed;
+            }
+        };
+        launch();
+        uint64_t seq = 1;
+        auto t_start = std::chrono::steady_clock::now();
+        auto timed_out = [&]() {
+            return std::chrono::steady_clock::now() - t_start > std::chrono::seconds(60);
+        };
+        for (int i = 0; i < nreq && !errors.load(); ++i) {
+            while (free_slots.empty() && !errors.load()) {
+                reap();
+                ensure_running();
+                if (timed_out()) {
+                    fail("no slot freed (in flight %llu)", (uint64_t)inflight);
+                    break;
+                }
+                std::this_thread::yield();
+            }
+            if (errors.load())
+                break;
+            if (i % 400 == 399)  // a pause longer than the idle timeout: the CTAs exit
+                std::this_thread::sleep_for(std::chrono::nanoseconds(3 * idle_ns));
+            const uint32_t d = free_slots.back();
+            free_slots.pop_back();
+            const Req &r = reqs[(size_t)i];
+            const uint64_t gn = ++gen[(size_t)d];
+            owner[(size_t)d] = i;
+            ++inflight;
+            QEntry &qe = queue[seq & (qsize - 1)];
+            qe.in = r.len ? 0x100000 : 0;
+            qe.out = r.len ? 0x200000 : 0;
+            qe.len = r.len;
+            qe.iv_hi = 0x0123456789abcdefull;
+            qe.iv_lo = r.iv_lo;
+            qe.gen = gn;
+            qe.key_slot = (uint32_t)r.key_slot;
+            qe.desc = (uint16_t)d;
+            qe.flags = 0;
+            __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
+            ++seq;
+            ensure_running();
+            reap();
+        }
+        while (inflight > 0 && !errors.load()) {
+            reap();
+            ensure_running();
+            if (timed_out()) {
+                fail("%llu requests never completed", (uint64_t)inflight);
+                break;
+            }
+            std::this_thread::yield();
+        }
+        __atomic_store_n(&ctrl[0], 1u, __ATOMIC_RELAXED);  // stop
+        for (auto &t : threads)
+            t.join();
+        uint64_t want_tiles = 0;
+        for (int i = 0; i < nreq; ++i) {
+            want_tiles += reqs[(size_t)i].ntiles;
+            if (!errors.load() && reqs[(size_t)i].completions.load() != 1)
+                fail("seq %llu completed %llu times", (uint64_t)i + 1, (uint64_t)reqs[(size_t)i].completions.load());
+        }
+        if (!errors.load() && tiles_done.load() != want_tiles)
+            fail("%llu tiles processed, %llu expected", tiles_done.load(), want_tiles);
+        std::printf("%s mode=%d ctas=%d slots=%d requests=%d completed=%d tiles=%llu launches=%d %s\n",
+                    errors.load() ? "FAIL" : "OK", mode, nctas, slots, nreq, completed,
+                    (unsigned long long)tiles_done.load(), launches, first_error);
+        std::free(recs);
+        std::free(queue);
+        return errors.load() ? 1 : 0;
+    }
+};
+
+}  // namespace
+
+int main(int argc, char **argv)
+{
+    if (argc != 8) {
+        std::fprintf(stderr, "usage: %s mode ctas slots requests tile_blocks idle_us seed\n", argv[0]);
+        return 2;
+    }
+    Sim s;
+    s.mode = std::atoi(argv[1]);
+    s.nctas = std::atoi(argv[2]);
+    s.slots = std::atoi(argv[3]);
+    s.nreq = std::atoi(argv[4]);
+    s.tile_blocks = std::atoi(argv[5]);
+    s.idle_ns = 1000ull * (uint64_t)std::atoll(argv[6]);
+    s.seed = (uint32_t)std::atoi(argv[7]);
+    return s.run();
+}

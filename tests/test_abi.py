@@ -103,3 +103,52 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(A, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         A.lib()
+
+
+# ctypes mirror (or numpy record) of each struct the header declares
+MIRRORS = {
+    "aes_launch_t": A.LaunchShape,
+    "aes_desc_t": A.Desc,
+    "aes_batch_opts_t": A.BatchOpts,
+    "offload_cfg_t": A.ServerCfg,
+    "offload_stats_t": A.ServerStats,
+    "aes_drive_result_t": A.DriveResult,
+    "aes_drive_opts_t": A.DriveOpts,
+    "cdet_run_cfg_t": A.CdetCfg,
+    "cdet_run_result_t": A.CdetResult,
+}
+C_FIELD = {("aes_desc_t", "inp"): "in"}  # names that are Python keywords
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets (the compiler's answer, from a C program built against the
+    header), so a field added on one side only cannot shift the others."""
+    drive = A.drive_dtype()
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "aesoffload.h"', "int main(void) {"]
+    for cname, cls in MIRRORS.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            cf = C_FIELD.get((cname, f), f)
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {cf}));')
+    lines.append('printf("aes_drive_req_t size %zu\\n", sizeof(aes_drive_req_t));')
+    for f in drive.names:
+        cf = "in" if f == "inp" else f
+        lines.append(f'printf("aes_drive_req_t {f} %zu\\n", offsetof(aes_drive_req_t, {cf}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", B.INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for line in out.splitlines():
+        t, f, v = line.split()
+        got[(t, f)] = int(v)
+    for cname, cls in MIRRORS.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+    assert got[("aes_drive_req_t", "size")] == drive.itemsize
+    for f in drive.names:
+        assert got[("aes_drive_req_t", f)] == drive.fields[f][1], f

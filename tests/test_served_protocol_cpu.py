@@ -1,0 +1,50 @@
+"""The served kernel's request protocol, run by host threads on the CPU.
+
+served_protocol.cuh holds the protocol (queue entries, dispatch into device
+records, tile claims by either the global cursor or per-request claim words,
+completion of a request's last tile) in code that compiles for the device
+and, with GCC atomics, for the host.  served_protocol_sim.cpp runs it with
+threads standing in for the resident CTAs (agent + worker each) against a
+producer that submits and reaps requests as offload_submit / offload_poll
+do, and checks that every tile is processed exactly once while its request
+owns the slot and that every request completes once with its status.  The
+settings mix slot reuse (down to one slot), more CTAs than cores, and idle
+timeouts short enough to make CTAs exit and be relaunched under load."""
+import os
+import subprocess
+
+import pytest
+
+from paper_2607_02630_gb300 import build as B
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def sim(tmp_path_factory):
+    nvcc = B._nvcc()
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+    exe = str(tmp_path_factory.mktemp("sim") / "served_protocol_sim")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", "-Wall", "-Wno-unknown-pragmas", "-I", B.INCLUDE,
+                    "-I", B.CSRC, "-I", cuda_inc, os.path.join(HERE, "served_protocol_sim.cpp"), "-o", exe],
+                   check=True)
+    return exe
+
+
+# ctas, slots, requests, tile_blocks (0 = per request), idle timeout us, seed
+CASES = [
+    (4, 32, 3000, 0, 2000, 7),
+    (4, 32, 2000, 64, 2000, 8),
+    (4, 32, 2000, 1024, 2000, 9),
+    (2, 4, 3000, 0, 2000, 11),
+    (16, 8, 3000, 64, 500, 12),
+    (12, 64, 4000, 0, 300, 13),
+    (3, 1, 1000, 0, 2000, 15),
+]
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["global_cursor", "per_request"])
+@pytest.mark.parametrize("case", CASES, ids=[f"c{c[0]}s{c[1]}t{c[3]}i{c[4]}" for c in CASES])
+def test_every_tile_once_every_request_once(sim, mode, case):
+    r = subprocess.run([sim, str(mode)] + [str(x) for x in case], capture_output=True, text=True, timeout=240)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
