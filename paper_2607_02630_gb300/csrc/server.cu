@@ -43,6 +43,14 @@
 // no new work for idle_timeout exits and its workers follow once the ring is
 // drained (the host relaunches the kernel on the next submit or poll), and
 // the stop flag ends every wait.
+//
+// claim_mode 1 replaces the global cursor with a claim word per request
+// record: agents walk the dispatched requests in order on their own, so
+// several requests are cut into tiles at once (cursor then holds `low`, the
+// oldest request that may have unclaimed tiles).  The protocol -- layouts,
+// dispatch, both claim modes, completion -- is in served_protocol.cuh; this
+// file holds the CTA structure (agent, shared-memory ring, workers) and the
+// host side.
 #include "../../include/aesoffload.h"
 #include "internal.h"
 #include "runtime.h"
