@@ -89,11 +89,12 @@ int offload_drive_ex(offload_server_t srv, const aes_drive_req_t *reqs, int n, i
         while (next < n || !pending.empty()) {
             if (seconds_since(t0) - last_progress > kNoProgressSeconds) {
                 sh.timed_out.store(true);
+                int failed = (int)pending.size();
                 for (auto &pr : pending)
                     latency_us[pr.second] = -1.0;
-                for (; next < n; next += nthreads)
+                for (; next < n; next += nthreads, ++failed)
                     latency_us[next] = -1.0;
-                sh.errors.fetch_add((int)pending.size());
+                sh.errors.fetch_add(failed);
                 break;
             }
             // blocking: a request is taken only once the previous one is done
@@ -161,7 +162,10 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
         cudaSetDevice(dev);
         cudaStream_t s = nullptr;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            sh.errors.fetch_add(1);
+            int failed = 0;
+            for (int i = k; i < n; i += nthreads, ++failed)
+                latency_us[i] = -1.0;
+            sh.errors.fetch_add(failed);
             return;
         }
         constexpr int kMaxPending = 256;
@@ -177,11 +181,12 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
         while (next < n || !pending.empty()) {
             if (seconds_since(t0) - last_progress > kNoProgressSeconds) {
                 sh.timed_out.store(true);
+                int failed = (int)pending.size();
                 for (auto &pr : pending)
                     latency_us[pr.second] = -1.0;
-                for (; next < n; next += nthreads)
+                for (; next < n; next += nthreads, ++failed)
                     latency_us[next] = -1.0;
-                sh.errors.fetch_add((int)pending.size());
+                sh.errors.fetch_add(failed);
                 break;
             }
             if (next < n && !free_ev.empty() && seconds_since(t0) >= reqs[next].arrival_s) {
