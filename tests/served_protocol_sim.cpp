@@ -6,10 +6,13 @@
 // them).  Checked: every tile of every request is processed exactly once
 // and while its request still owns the slot, every request completes once
 // with the right status, zero-length and rejected requests complete at
-// dispatch, and idle exits, relaunches and the stop flag behave.  Logic
-// only: host memory ordering is not the GPU's.
+// dispatch, emulated offloads take one tile, and idle exits and relaunches
+// behave.  Scenario 1 raises the stop flag with work in flight (every CTA
+// must exit); scenario 2 queues an entry naming a slot the host never
+// issues (the CTAs must stop with ERROR).  Logic only: host memory ordering
+// is not the GPU's.
 //
-// usage: served_protocol_sim mode ctas slots requests tile_blocks idle_us seed
+// usage: served_protocol_sim mode ctas slots requests tile_blocks idle_us seed [scenario]
 #include "served_protocol.cuh"
 
 #include <atomic>
@@ -38,6 +41,7 @@ struct Req {
     uint64_t iv_lo = 0;
     int key_slot = 0;
     bool valid = true;
+    bool emulated = false;
     uint32_t ntiles = 0;                       // expected tile count
     std::unique_ptr<std::atomic<uint8_t>[]> marks;
     std::atomic<int> completions{0};
@@ -56,7 +60,7 @@ struct Cta {
 };
 
 struct Sim {
-    int mode = 0, nctas = 4, slots = 64, nreq = 2000, tile_blocks = 0;
+    int mode = 0, nctas = 4, slots = 64, nreq = 2000, tile_blocks = 0, scenario = 0;
     uint64_t idle_ns = 2000000;
     uint32_t seed = 1;
 
@@ -183,7 +187,7 @@ struct Sim {
                 break;
         }
         c->exit_code.store(code);
-        if (code & kExitError)
+        if ((code & kExitError) && scenario != 2)
             fail("agent stopped with ERROR");
         __atomic_fetch_or(P.kstatus, code, __ATOMIC_RELAXED);
         c->agent_done.store(true);
@@ -283,12 +287,15 @@ struct Sim {
                 r.len = 1 + g() % 8192;
             else if (kind < 18)
                 r.len = 1 + g() % (256u << 10);
-            else
+            else if (kind < 19)
                 r.len = 1 + g() % (2u << 20);
+            else
+                r.len = 1 + g() % 5000;  // emulated: a duration in ns
+            r.emulated = kind == 19;
             r.iv_lo = g();
             r.key_slot = (int)(g() % kMaxKeys);
-            r.valid = key_nr[(size_t)r.key_slot] != 0;
-            r.ntiles = r.valid ? tile_count(r.len, r.iv_lo) : 0;
+            r.valid = r.emulated || key_nr[(size_t)r.key_slot] != 0;
+            r.ntiles = r.emulated ? 1 : (r.valid ? tile_count(r.len, r.iv_lo) : 0);
             r.marks.reset(new std::atomic<uint8_t>[r.ntiles ? r.ntiles : 1]);
             for (uint32_t t = 0; t < r.ntiles; ++t)
                 r.marks[t].store(0);
@@ -347,19 +354,21 @@ struct Sim {
             owner[(size_t)d] = i;
             ++inflight;
             QEntry &qe = queue[seq & (qsize - 1)];
-            qe.in = r.len ? 0x100000 : 0;
-            qe.out = r.len ? 0x200000 : 0;
+            qe.in = r.len && !r.emulated ? 0x100000 : 0;
+            qe.out = r.len && !r.emulated ? 0x200000 : 0;
             qe.len = r.len;
             qe.iv_hi = 0x0123456789abcdefull;
             qe.iv_lo = r.iv_lo;
             qe.gen = gn;
             qe.key_slot = (uint32_t)r.key_slot;
             qe.desc = (uint16_t)d;
-            qe.flags = 0;
+            qe.flags = r.emulated ? (uint16_t)kFlagEmulated : 0;
             __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
             ++seq;
             ensure_running();
             reap();
+            if (scenario && i == nreq / 2)
+                return finish_scenario(seq, inflight);
         }
         while (inflight > 0 && !errors.load()) {
             reap();
@@ -388,14 +397,59 @@ struct Sim {
         std::free(queue);
         return errors.load() ? 1 : 0;
     }
+
+    // Wait (bounded) until every stand-in CTA has exited, then join them.
+    bool all_exit(double seconds)
+    {
+        const auto t0 = std::chrono::steady_clock::now();
+        while (live.load() > 0) {
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::duration<double>(seconds))
+                return false;
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+        for (auto &t : threads)
+            t.join();
+        threads.clear();
+        return true;
+    }
+
+    // Scenario 1: stop with requests in flight.  Scenario 2: an entry the
+    // host never writes (slot beyond nslots) stops the CTAs with ERROR.
+    int finish_scenario(uint64_t seq, int inflight)
+    {
+        const char *what = "stop";
+        if (scenario == 1) {
+            __atomic_store_n(&ctrl[0], 1u, __ATOMIC_RELAXED);
+            if (!all_exit(10.0))
+                fail("CTAs still running 10 s after the stop flag (in flight %llu)", (uint64_t)inflight);
+            else if (!(__atomic_load_n(&ctrl[1], __ATOMIC_RELAXED) & kExitStop))
+                fail("no CTA reported STOP (status %llu)", __atomic_load_n(&ctrl[1], __ATOMIC_RELAXED));
+        } else {
+            what = "bad entry";
+            QEntry &qe = queue[seq & (qsize - 1)];
+            std::memset(&qe, 0, sizeof(qe));
+            qe.desc = 0xffff;
+            __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
+            if (!all_exit(10.0 + 2e-9 * (double)idle_ns))
+                fail("CTAs still running after an invalid queue entry");
+            else if (!(__atomic_load_n(&ctrl[1], __ATOMIC_RELAXED) & kExitError))
+                fail("no CTA reported ERROR (status %llu)", __atomic_load_n(&ctrl[1], __ATOMIC_RELAXED));
+            __atomic_store_n(&ctrl[0], 1u, __ATOMIC_RELAXED);
+        }
+        std::printf("%s mode=%d scenario=%s ctas=%d tiles=%llu status=%u %s\n", errors.load() ? "FAIL" : "OK",
+                    mode, what, nctas, (unsigned long long)tiles_done.load(), ctrl[1], first_error);
+        std::free(recs);
+        std::free(queue);
+        return errors.load() ? 1 : 0;
+    }
 };
 
 }  // namespace
 
 int main(int argc, char **argv)
 {
-    if (argc != 8) {
-        std::fprintf(stderr, "usage: %s mode ctas slots requests tile_blocks idle_us seed\n", argv[0]);
+    if (argc != 8 && argc != 9) {
+        std::fprintf(stderr, "usage: %s mode ctas slots requests tile_blocks idle_us seed [scenario]\n", argv[0]);
         return 2;
     }
     Sim s;
@@ -406,5 +460,6 @@ int main(int argc, char **argv)
     s.tile_blocks = std::atoi(argv[5]);
     s.idle_ns = 1000ull * (uint64_t)std::atoll(argv[6]);
     s.seed = (uint32_t)std::atoi(argv[7]);
+    s.scenario = argc == 9 ? std::atoi(argv[8]) : 0;
     return s.run();
 }

@@ -48,3 +48,23 @@ CASES = [
 def test_every_tile_once_every_request_once(sim, mode, case):
     r = subprocess.run([sim, str(mode)] + [str(x) for x in case], capture_output=True, text=True, timeout=240)
     assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["global_cursor", "per_request"])
+@pytest.mark.parametrize("case", [(4, 32, 3000, 0, 2000, 22), (8, 4, 2000, 64, 500, 24)], ids=["wide", "tight"])
+def test_stop_flag_with_work_in_flight(sim, mode, case):
+    """Every stand-in CTA exits once the stop flag is raised mid-run, with
+    no tile processed twice."""
+    r = subprocess.run([sim, str(mode)] + [str(x) for x in case] + ["1"], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["global_cursor", "per_request"])
+def test_invalid_queue_entry_stops_with_error(sim, mode):
+    """A queue entry naming a slot the host never issues stops the CTAs with
+    status ERROR instead of leaving them waiting on it."""
+    r = subprocess.run([sim, str(mode), "4", "32", "3000", "0", "2000", "23", "2"], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
+    assert "status=" in r.stdout and int(r.stdout.split("status=")[1].split()[0]) & 4
