@@ -504,13 +504,14 @@ SRV_FN bool exhausted(const SrvParams &p, uint32_t s)
     return seq_after(vs, s);  // newer: s was reaped; older: s's claim word not seen yet
 }
 
-// The caller found request s without unclaimed tiles: move low from s to
-// s + 1, and on over every following request that is exhausted too.  A
-// failed CAS means low is not s (behind it: whoever moves low to s goes on
-// from there, and waiting agents repeat the check; ahead: nothing to do).
-// The fences order the claim word accesses against the CAS on low (the
-// caller's claim, then its CAS; another agent's CAS, then its look at the
-// claim word), so that one of the two sees the other.
+// Request s has no unclaimed tiles any more (the caller took its last ones,
+// or it has none): move low from s to s + 1, and on over every following
+// request that is exhausted too.  A failed CAS means low is not s (behind
+// it: whoever moves low to s goes on from there, and waiting agents repeat
+// the check; ahead: nothing to do).  The fences order the claim word
+// accesses against the CAS on low (the caller's last claim, then its CAS;
+// another agent's CAS, then its look at the claim word), so that one of the
+// two sees the other.
 SRV_FN void help_low(const SrvParams &p, uint32_t s)
 {
     fence_gpu();
@@ -615,7 +616,11 @@ SRV_FN uint32_t claim_pr(const SrvParams &p, uint32_t &cur, uint64_t &last_work,
                     }
                 }
             }
-            help_low(p, cur);  // cur has no tiles left
+            // cur has no tiles left.  Moving low on is the job of the agent
+            // that took the last tiles (above); a request without tiles has
+            // none, so its visitors do it, once low has reached it.
+            if (nt == 0 && (uint32_t)ld_relaxed_gpu(p.cursor) == cur)
+                help_low(p, cur);
             cur = (cur + 1) & kSeqMask;
             backoff = 32;
             continue;
