@@ -645,6 +645,15 @@ def conflict_study(args, rank, local):
                             "enforce_vs_lock": round(rows["enforce"]["req_per_s"] / rows["coarse_lock"]["req_per_s"], 2),
                             "enforce_vs_unprotected": round(rows["enforce"]["req_per_s"]
                                                             / rows["unprotected"]["req_per_s"], 3)})
+        # the paper's taxonomy of shared state: detection on each pattern,
+        # over the 1 MiB served offload (only the shared aggregate is hazardous)
+        pats = {A.CDET_PATTERN_SHARED: "shared_unlocked", A.CDET_PATTERN_READONLY: "read_only",
+                A.CDET_PATTERN_PER_CONN: "per_connection", A.CDET_PATTERN_LOCKED: "lock_protected"}
+        taxonomy = {}
+        for pat, name in pats.items():
+            r = A.conflict_run(A.CDET_DETECT, handlers, requests, 64, server=srv, key_slot=ks, buf_in=src,
+                               buf_out=dst, nbytes=min(sizes), pattern=pat)
+            taxonomy[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
         n1 = 5000
         off = A.conflict_run(A.CDET_UNPROTECTED, 1, n1, 1, offload_ns=0)
         on = A.conflict_run(A.CDET_DETECT, 1, n1, 1, offload_ns=0)
@@ -653,6 +662,7 @@ def conflict_study(args, rank, local):
         srv.close()
     out = {"metric": "shared-counter read-modify-write across a GPU offload: lost updates and req/s by guard",
            "unit": "req/s", "handlers": handlers, "counters": 64, "requests": requests, "studies": studies,
+           "taxonomy_detect": taxonomy, "taxonomy_bytes": min(sizes),
            "guarded_write_cost_us": round(fault_us, 2),
            "guarded_write_cost_how": "1 handler, no offload: (detect - unprotected) time per request = one write "
                                      "fault + two mprotect calls, in this CUDA process"}

@@ -398,6 +398,14 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
 #define CDET_DETECT 2      /* overlap, conflicts counted, not prevented */
 #define CDET_ENFORCE 3     /* overlap, conflicting handlers re-run serialized */
 
+/* Shared-state patterns of the synthetic server (the paper's taxonomy,
+ * Sec. 5): only the first is hazardous under overlap. */
+#define CDET_PATTERN_SHARED 0     /* unlocked read-modify-write of a shared counter across the offload */
+#define CDET_PATTERN_READONLY 1   /* the shared counter is only read */
+#define CDET_PATTERN_PER_CONN 2   /* each handler (connection) updates a counter of its own;
+                                     needs counters >= handlers */
+#define CDET_PATTERN_LOCKED 3     /* the application holds a lock across its read-modify-write */
+
 typedef struct {
     int handlers;
     int requests;
@@ -410,10 +418,12 @@ typedef struct {
     const void *buf_in;
     void *buf_out;
     size_t bytes;
+    int pattern;            /* CDET_PATTERN_*; 0 = the shared unlocked counter */
 } cdet_run_cfg_t;
 
 typedef struct {
-    uint64_t final_count;   /* sum of the counters (requests if no update was lost) */
+    uint64_t final_count;   /* sum of the counters (requests if no update was lost);
+                               CDET_PATTERN_READONLY: requests whose read completed */
     uint64_t lost_updates;  /* requests - final_count */
     uint64_t conflicts;     /* write faults on a page modified during the writer's park */
     uint64_t restarts;      /* handlers re-run serialized (CDET_ENFORCE) */

@@ -14,7 +14,13 @@
 // cooperative handlers (ucontext fibers on the calling thread, one event
 // loop) serve `requests` requests; request i reads shared counter
 // c(i) (one of `counters`, `counters_per_page` to a page), parks at an
-// offload, and writes the counter back incremented.  Modes:
+// offload, and writes the counter back incremented.  The paper sorts the
+// shared state of offload-adjacent servers into four patterns, of which
+// only this unlocked shared aggregate is hazardous under overlap; the
+// other three are selectable too (`pattern`), to check that the detector
+// stays silent on them: the counter is only read; each handler (one per
+// connection) updates a counter of its own; the application holds a lock
+// from the read to the write.  Modes:
 //   UNPROTECTED  overlap, nothing guards the counters (updates get lost);
 //   LOCK         one coarse lock held from the read to the write, i.e.
 //                across the offload (serializes the offloads it protects);
@@ -64,6 +70,7 @@ struct Fiber {
     bool snap_valid = false;    // has parked during the current request
     uint64_t snapshot = 0;      // version clock when it last parked
     uint64_t ticket = 0;        // offload in flight (server)
+    uint64_t reads = 0;         // CDET_PATTERN_READONLY: reads completed
     clk::time_point deadline;   // offload in flight (host timer)
     int dirty_lo = 0, dirty_hi = -1;  // pages this handler unprotected: within [lo, hi]
 };
@@ -218,7 +225,9 @@ void serve(Run &r, Fiber &f, int req)
     h = (h ^ (h >> 30)) * 0xBF58476D1CE4E5B9ull;
     h = (h ^ (h >> 27)) * 0x94D049BB133111EBull;
     h ^= h >> 31;
-    const int c = (int)(h % (uint64_t)r.cfg.counters);
+    const int pattern = r.cfg.pattern;
+    const int c = pattern == CDET_PATTERN_PER_CONN ? f.id : (int)(h % (uint64_t)r.cfg.counters);
+    const bool locked = r.cfg.mode == CDET_LOCK || pattern == CDET_PATTERN_LOCKED;
     f.serialized = false;
     if (sigsetjmp(f.restart, 1)) {
         // restarted after a conflict (the stale write faulted before it
@@ -227,13 +236,16 @@ void serve(Run &r, Fiber &f, int req)
         f.serialized = true;
     }
     f.snap_valid = false;
-    if (r.cfg.mode == CDET_LOCK)
+    if (locked)
         acquire_lock(r, f);
     volatile uint64_t *ctr = counter_ptr(r, c);
     const uint64_t v = *ctr;  // read
     offload(r, f, req);       // park
-    *ctr = v + 1;             // write (may fault)
-    if (r.cfg.mode == CDET_LOCK)
+    if (pattern == CDET_PATTERN_READONLY)
+        ++f.reads;
+    else
+        *ctr = v + 1;         // write (may fault)
+    if (locked)
         release_lock(r);
     protect_dirty(r, f);
     f.snap_valid = false;
@@ -261,7 +273,9 @@ int cdet_run(const cdet_run_cfg_t *cfg, cdet_run_result_t *res)
 {
     if (!cfg || !res || cfg->handlers < 1 || cfg->handlers > 4096 || cfg->requests < 0 || cfg->counters < 1 ||
         cfg->counters_per_page < 1 || cfg->counters_per_page > 64 || cfg->mode < CDET_UNPROTECTED ||
-        cfg->mode > CDET_ENFORCE || (cfg->bytes && (!cfg->srv || !cfg->buf_in || !cfg->buf_out)))
+        cfg->mode > CDET_ENFORCE || (cfg->bytes && (!cfg->srv || !cfg->buf_in || !cfg->buf_out)) ||
+        cfg->pattern < CDET_PATTERN_SHARED || cfg->pattern > CDET_PATTERN_LOCKED ||
+        (cfg->pattern == CDET_PATTERN_PER_CONN && cfg->counters < cfg->handlers))
         return AES_EINVAL;
     if (g_run)
         return AES_EINVAL;  // one run at a time
@@ -333,6 +347,8 @@ int cdet_run(const cdet_run_cfg_t *cfg, cdet_run_result_t *res)
         mprotect(r.region, r.region_bytes, PROT_READ | PROT_WRITE);
     for (int c = 0; c < cfg->counters; ++c)
         total += *counter_ptr(r, c);
+    for (auto &f : r.fibers)
+        total += f.reads;
     if (r.detector && !r.error)
         sigaction(SIGSEGV, &g_prev_segv, nullptr);
     g_run = nullptr;

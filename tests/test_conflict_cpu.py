@@ -77,3 +77,32 @@ def test_bad_arguments():
         A.conflict_run(7)
     with pytest.raises(A.AesError):
         A.conflict_run(A.CDET_LOCK, counters_per_page=65)
+
+
+@pytest.mark.parametrize("pattern", [A.CDET_PATTERN_READONLY, A.CDET_PATTERN_PER_CONN, A.CDET_PATTERN_LOCKED],
+                         ids=["read_only", "per_connection", "lock_protected"])
+def test_safe_patterns_raise_no_conflict(pattern):
+    """The three shared-state patterns the paper finds safe under overlap
+    (read-only, per-connection, lock-protected) lose nothing and make the
+    detector report nothing; the hazardous one, on the same settings, does
+    both."""
+    r = A.conflict_run(A.CDET_DETECT, handlers=16, requests=2000, counters=64, pattern=pattern)
+    assert r["conflicts"] == 0 and r["lost_updates"] == 0 and r["final_count"] == 2000, r
+    hazard = A.conflict_run(A.CDET_DETECT, handlers=16, requests=2000, counters=64)
+    assert hazard["conflicts"] > 0 and hazard["lost_updates"] > 0
+
+
+def test_per_connection_counters_sharing_a_page_are_flagged():
+    """Per-connection counters packed onto one page lose no update but are
+    flagged: the detector works at page granularity (conservative)."""
+    r = A.conflict_run(A.CDET_DETECT, handlers=16, requests=2000, counters=64, counters_per_page=64,
+                       pattern=A.CDET_PATTERN_PER_CONN)
+    assert r["lost_updates"] == 0 and r["final_count"] == 2000
+    assert r["conflicts"] > 0
+
+
+def test_pattern_arguments():
+    with pytest.raises(A.AesError):
+        A.conflict_run(A.CDET_DETECT, pattern=4)
+    with pytest.raises(A.AesError):  # per-connection needs a counter per handler
+        A.conflict_run(A.CDET_DETECT, handlers=16, counters=8, pattern=A.CDET_PATTERN_PER_CONN)

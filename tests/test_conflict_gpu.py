@@ -49,3 +49,17 @@ def test_enforce_with_real_aes_offload(cuda, aes, ncpu):
         np.testing.assert_array_equal(out, oracle.ctr_mt(key, 128, hits[0], data, ncpu))
     finally:
         assert srv.close() == aes.AES_OK
+
+
+@pytest.mark.parametrize("pattern", [A.CDET_PATTERN_READONLY, A.CDET_PATTERN_PER_CONN, A.CDET_PATTERN_LOCKED],
+                         ids=["read_only", "per_connection", "lock_protected"])
+def test_safe_patterns_with_served_emulated_offload(cuda, aes, pattern):
+    """Over a served (emulated) offload, the shared-state patterns the paper
+    finds safe raise no conflict and lose nothing under detection."""
+    srv = aes.Server(slots=64, max_keys=1, ctas=16, idle_timeout_us=500_000)
+    try:
+        r = aes.conflict_run(aes.CDET_DETECT, handlers=16, requests=1000, counters=16, offload_ns=20_000,
+                             server=srv, pattern=pattern)
+        assert r["conflicts"] == 0 and r["lost_updates"] == 0 and r["final_count"] == 1000, r
+    finally:
+        assert srv.close() == aes.AES_OK
