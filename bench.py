@@ -640,9 +640,15 @@ def conflict_study(args, rank, local):
             for mode, name in names.items():
                 r = run(mode, requests)
                 rows[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+            for mode, name in ((A.CDET_DETECT, "detect_emulated_stores"), (A.CDET_ENFORCE, "enforce_emulated_stores")):
+                r = A.conflict_run(mode, handlers, requests, 64, server=srv, key_slot=ks, buf_in=src, buf_out=dst,
+                                   nbytes=nbytes, emulate_stores=True)
+                rows[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
             studies.append({"offload": f"served AES-128-CTR, {nbytes} bytes per request, payload in HBM",
                             "rows": rows,
                             "enforce_vs_lock": round(rows["enforce"]["req_per_s"] / rows["coarse_lock"]["req_per_s"], 2),
+                            "enforce_emulated_vs_lock": round(rows["enforce_emulated_stores"]["req_per_s"]
+                                                              / rows["coarse_lock"]["req_per_s"], 2),
                             "enforce_vs_unprotected": round(rows["enforce"]["req_per_s"]
                                                             / rows["unprotected"]["req_per_s"], 3)})
         # the paper's taxonomy of shared state: detection on each pattern,
@@ -658,12 +664,16 @@ def conflict_study(args, rank, local):
         off = A.conflict_run(A.CDET_UNPROTECTED, 1, n1, 1, offload_ns=0)
         on = A.conflict_run(A.CDET_DETECT, 1, n1, 1, offload_ns=0)
         fault_us = (on["elapsed_s"] - off["elapsed_s"]) / n1 * 1e6
+        on_e = A.conflict_run(A.CDET_DETECT, 1, n1, 1, offload_ns=0, emulate_stores=True)
+        fault_emu_us = (on_e["elapsed_s"] - off["elapsed_s"]) / n1 * 1e6
+        selftest = A.store_selftest(6000)
     finally:
         srv.close()
     out = {"metric": "shared-counter read-modify-write across a GPU offload: lost updates and req/s by guard",
            "unit": "req/s", "handlers": handlers, "counters": 64, "requests": requests, "studies": studies,
            "taxonomy_detect": taxonomy, "taxonomy_bytes": min(sizes),
            "guarded_write_cost_us": round(fault_us, 2),
+           "guarded_write_cost_emulated_us": round(fault_emu_us, 2), "store_emulation_selftest": selftest,
            "guarded_write_cost_how": "1 handler, no offload: (detect - unprotected) time per request = one write "
                                      "fault + two mprotect calls, in this CUDA process"}
     if rank == 0:

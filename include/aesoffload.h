@@ -419,6 +419,13 @@ typedef struct {
     void *buf_out;
     size_t bytes;
     int pattern;            /* CDET_PATTERN_*; 0 = the shared unlocked counter */
+    int emulate_stores;     /* detector: keep the pages read-only and perform each
+                               faulting store in the fault handler (through a
+                               second, writable mapping), so a guarded write
+                               changes no protection; stores it cannot decode
+                               (only plain general-register stores are: x86-64
+                               MOV, AArch64 STR/STUR) unprotect the page as
+                               when this is 0 */
 } cdet_run_cfg_t;
 
 typedef struct {
@@ -428,9 +435,20 @@ typedef struct {
     uint64_t conflicts;     /* write faults on a page modified during the writer's park */
     uint64_t restarts;      /* handlers re-run serialized (CDET_ENFORCE) */
     double elapsed_s;
+    uint64_t emulated_stores; /* guarded writes performed by the fault handler */
+    uint64_t protect_calls;   /* protection changes during the run (setup and teardown excluded) */
 } cdet_run_result_t;
 
 int cdet_run(const cdet_run_cfg_t *cfg, cdet_run_result_t *res);
+
+/* Self-test of the detector's store emulation on this CPU: `rounds` guarded
+ * stores of 8, 16, 32 and 64 bits at run-time offsets of a read-only
+ * region, each performed by the fault handler where it can decode the
+ * instruction (else by unprotecting the page), checked against a plain
+ * shadow copy.  *emulated / *fallbacks: stores performed each way.
+ * AES_OK if the region matches the shadow, AES_EDESC if not; AES_EINVAL
+ * (bad arguments, or a cdet_run in progress), AES_ENOMEM. */
+int cdet_store_selftest(int rounds, uint64_t *emulated, uint64_t *fallbacks);
 
 #ifdef __cplusplus
 }

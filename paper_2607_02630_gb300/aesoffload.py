@@ -78,12 +78,14 @@ class CdetCfg(ctypes.Structure):
     _fields_ = [("handlers", ctypes.c_int), ("requests", ctypes.c_int), ("counters", ctypes.c_int),
                 ("counters_per_page", ctypes.c_int), ("mode", ctypes.c_int), ("offload_ns", ctypes.c_uint64),
                 ("srv", ctypes.c_void_p), ("key_slot", ctypes.c_int), ("buf_in", ctypes.c_void_p),
-                ("buf_out", ctypes.c_void_p), ("bytes", ctypes.c_size_t), ("pattern", ctypes.c_int)]
+                ("buf_out", ctypes.c_void_p), ("bytes", ctypes.c_size_t), ("pattern", ctypes.c_int),
+                ("emulate_stores", ctypes.c_int)]
 
 
 class CdetResult(ctypes.Structure):
     _fields_ = [("final_count", ctypes.c_uint64), ("lost_updates", ctypes.c_uint64), ("conflicts", ctypes.c_uint64),
-                ("restarts", ctypes.c_uint64), ("elapsed_s", ctypes.c_double)]
+                ("restarts", ctypes.c_uint64), ("elapsed_s", ctypes.c_double),
+                ("emulated_stores", ctypes.c_uint64), ("protect_calls", ctypes.c_uint64)]
 
 
 CDET_UNPROTECTED, CDET_LOCK, CDET_DETECT, CDET_ENFORCE = 0, 1, 2, 3
@@ -139,6 +141,8 @@ _SIGS = {
     "offload_drive_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(DriveOpts), ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
     "cdet_run": (ctypes.c_int, [ctypes.POINTER(CdetCfg), ctypes.POINTER(CdetResult)]),
+    "cdet_store_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ctypes.c_uint64)]),
     "offload_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
     "aes_ctr_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -450,16 +454,26 @@ def drive_per_call(ctxs, reqs, nthreads: int = 8):
 
 def conflict_run(mode: int, handlers: int = 16, requests: int = 4000, counters: int = 64, counters_per_page: int = 1,
                  offload_ns: int = 50_000, server: "Server | None" = None, key_slot: int = 0, buf_in=0, buf_out=0,
-                 nbytes: int = 0, pattern: int = 0) -> dict:
+                 nbytes: int = 0, pattern: int = 0, emulate_stores: bool = False) -> dict:
     """cdet_run: the conflict detector's synthetic server (read a shared
     counter, park at an offload, write it back incremented) in one of the
     CDET_* modes, with the shared state in one of the CDET_PATTERN_*
     patterns; returns the result as a dict (requests/s added)."""
     cfg = CdetCfg(int(handlers), int(requests), int(counters), int(counters_per_page), int(mode), int(offload_ns),
                   server.handle if server else None, int(key_slot), ptr(buf_in) or None, ptr(buf_out) or None,
-                  int(nbytes), int(pattern))
+                  int(nbytes), int(pattern), int(bool(emulate_stores)))
     res = CdetResult()
     _check(lib().cdet_run(ctypes.byref(cfg), ctypes.byref(res)), "cdet_run")
     out = {f: getattr(res, f) for f, _ in CdetResult._fields_}
     out["req_per_s"] = requests / res.elapsed_s if res.elapsed_s > 0 else 0.0
     return out
+
+
+def store_selftest(rounds: int = 6000) -> dict:
+    """cdet_store_selftest: guarded stores of every width on this CPU,
+    performed by the detector's fault handler where it decodes them; raises
+    if the region does not match its shadow copy."""
+    emulated, fallbacks = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().cdet_store_selftest(int(rounds), ctypes.byref(emulated), ctypes.byref(fallbacks)),
+           "cdet_store_selftest")
+    return {"emulated": emulated.value, "fallbacks": fallbacks.value}

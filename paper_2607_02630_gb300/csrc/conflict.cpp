@@ -41,6 +41,12 @@
 // restart is a siglongjmp from the fault handler to the request's start,
 // taken on the handler's own stack; it suits handlers whose writes before
 // the conflicting one may be repeated (true of the workload here).
+//
+// With cfg.emulate_stores the pages are never unprotected: the fault
+// handler performs the store itself through a writable alias of the region
+// (see "store emulation" below), so every write faults and a page also
+// records which handler stamped it (a handler's own later writes are no
+// conflict).
 #include "../../include/aesoffload.h"
 
 #include <chrono>
@@ -82,6 +88,9 @@ struct Run {
     size_t region_bytes = 0;
     int npages = 0;
     std::vector<uint64_t> page_version;
+    std::vector<int> page_writer;  // handler whose write stamped the page (-1 none)
+    uint8_t *alias = nullptr;      // writable second mapping of the region (store emulation)
+    uint64_t emulated = 0, protect_calls = 0;
     uint64_t clock = 0;
     std::vector<Fiber> fibers;
     Fiber *current = nullptr;
@@ -108,12 +117,131 @@ uint64_t *counter_ptr(Run &r, int c)
 // spans its unprotected pages restores the invariant, however many they are.
 void protect_dirty(Run &r, Fiber &f)
 {
-    if (f.dirty_hi >= f.dirty_lo)
+    if (f.dirty_hi >= f.dirty_lo) {
         mprotect(r.region + (size_t)f.dirty_lo * (size_t)r.page,
                  (size_t)(f.dirty_hi - f.dirty_lo + 1) * (size_t)r.page, PROT_READ);
+        ++r.protect_calls;
+    }
     f.dirty_lo = 0;
     f.dirty_hi = -1;
 }
+
+// ---- store emulation (cfg.emulate_stores) --------------------------------
+// The shared pages stay read-only for the whole run.  The fault handler
+// performs the faulting store itself, through a second, writable mapping
+// of the same memory, and steps the program counter past it.  A guarded
+// write then costs one fault and no protection change; a protection change
+// is the expensive part in a process that shares its page tables with a GPU.
+// Decoded are the plain general-register stores a compiler emits for an
+// aggregate update:
+//   x86-64: MOV r/m8|16|32|64, r (opcodes 88 / 89, optional 66 and REX);
+//   AArch64: STR / STUR / STTR of 8..64-bit general registers (immediate
+//   unsigned offset, unscaled, pre- and post-index with base write-back,
+//   register offset).
+// Anything else (vector, pair, atomic and exclusive stores) falls back to
+// unprotecting the page.
+struct Store {
+    uint64_t value = 0;
+    int size = 0;        // bytes stored
+    int len = 0;         // instruction bytes
+    int wb_reg = -1;     // AArch64 base register written back (31 = SP), -1 none
+    int64_t wb_delta = 0;
+};
+
+#if defined(__x86_64__)
+int x86_greg(int n)
+{
+    static const int map[16] = {REG_RAX, REG_RCX, REG_RDX, REG_RBX, REG_RSP, REG_RBP, REG_RSI, REG_RDI,
+                                REG_R8,  REG_R9,  REG_R10, REG_R11, REG_R12, REG_R13, REG_R14, REG_R15};
+    return map[n & 15];
+}
+
+bool decode_store(const ucontext_t *uc, Store *st)
+{
+    const greg_t *g = uc->uc_mcontext.gregs;
+    const uint8_t *ip = reinterpret_cast<const uint8_t *>(g[REG_RIP]);
+    int i = 0;
+    bool op16 = false;
+    if (ip[i] == 0x66) {
+        op16 = true;
+        ++i;
+    }
+    uint8_t rex = 0;
+    if ((ip[i] & 0xF0) == 0x40)
+        rex = ip[i++];
+    const uint8_t op = ip[i++];
+    if (op != 0x88 && op != 0x89)
+        return false;
+    const uint8_t modrm = ip[i++];
+    const int mod = modrm >> 6, rm = modrm & 7, reg = (modrm >> 3) & 7;
+    if (mod == 3)
+        return false;  // register destination: not a store
+    if (rm == 4) {     // SIB byte; base 101 with mod 00 means disp32 and no base
+        const uint8_t sib = ip[i++];
+        if (mod == 0 && (sib & 7) == 5)
+            i += 4;
+    } else if (mod == 0 && rm == 5) {
+        i += 4;  // RIP-relative disp32
+    }
+    if (mod == 1)
+        i += 1;
+    else if (mod == 2)
+        i += 4;
+    if (op == 0x88) {
+        st->size = 1;
+        if (!rex && reg >= 4)  // AH, CH, DH, BH
+            st->value = (uint64_t)g[x86_greg(reg - 4)] >> 8;
+        else
+            st->value = (uint64_t)g[x86_greg(reg | ((rex & 4) ? 8 : 0))];
+    } else {
+        st->size = (rex & 8) ? 8 : (op16 ? 2 : 4);
+        st->value = (uint64_t)g[x86_greg(reg | ((rex & 4) ? 8 : 0))];
+    }
+    st->len = i;
+    return true;
+}
+
+void retire_store(ucontext_t *uc, const Store &st)
+{
+    uc->uc_mcontext.gregs[REG_RIP] += st.len;
+}
+#elif defined(__aarch64__)
+bool decode_store(const ucontext_t *uc, Store *st)
+{
+    const uint32_t insn = *reinterpret_cast<const uint32_t *>(uc->uc_mcontext.pc);
+    const int rt = (int)(insn & 31), rn = (int)((insn >> 5) & 31);
+    if ((insn & 0x3FC00000u) == 0x39000000u) {
+        // STR (immediate, unsigned offset): size 111 0 01 00 imm12 Rn Rt
+    } else if ((insn & 0x3FE00000u) == 0x38000000u) {
+        // STUR / STR post-index / STTR / STR pre-index: size 111 0 00 00 0 imm9 idx Rn Rt
+        const uint32_t idx = (insn >> 10) & 3;
+        if (idx == 1 || idx == 3) {
+            st->wb_reg = rn;
+            st->wb_delta = (int64_t)((int32_t)(insn << 11) >> 23);  // imm9, sign-extended
+        }
+    } else if ((insn & 0x3FE00C00u) == 0x38200800u) {
+        // STR (register offset): size 111 0 00 00 1 Rm option S 10 Rn Rt
+    } else {
+        return false;
+    }
+    st->size = 1 << (insn >> 30);
+    st->value = rt == 31 ? 0 : (uint64_t)uc->uc_mcontext.regs[rt];  // register 31 is XZR here
+    st->len = 4;
+    return true;
+}
+
+void retire_store(ucontext_t *uc, const Store &st)
+{
+    if (st.wb_reg == 31)
+        uc->uc_mcontext.sp += (uint64_t)st.wb_delta;
+    else if (st.wb_reg >= 0)
+        uc->uc_mcontext.regs[st.wb_reg] += (uint64_t)st.wb_delta;
+    uc->uc_mcontext.pc += (uint64_t)st.len;
+}
+#else
+bool decode_store(const ucontext_t *, Store *) { return false; }
+void retire_store(ucontext_t *, const Store &) {}
+#endif
 
 void on_fault(int sig, siginfo_t *si, void *uc)
 {
@@ -128,7 +256,10 @@ void on_fault(int sig, siginfo_t *si, void *uc)
     }
     Fiber &f = *r->current;
     const int p = (int)((size_t)(a - r->region) / (size_t)r->page);
-    if (f.snap_valid && r->page_version[(size_t)p] > f.snapshot) {
+    // a conflict: the page changed during this handler's park, by another
+    // handler (with store emulation every write faults, the handler's own
+    // later writes included)
+    if (f.snap_valid && r->page_version[(size_t)p] > f.snapshot && r->page_writer[(size_t)p] != f.id) {
         ++r->conflicts;
         if (r->cfg.mode == CDET_ENFORCE) {
             ++r->restarts;
@@ -136,7 +267,18 @@ void on_fault(int sig, siginfo_t *si, void *uc)
         }
     }
     r->page_version[(size_t)p] = ++r->clock;
+    r->page_writer[(size_t)p] = f.id;
+    Store st;
+    ucontext_t *ctx = static_cast<ucontext_t *>(uc);
+    if (r->alias && decode_store(ctx, &st) &&
+        (size_t)(a - r->region) % (size_t)r->page + (size_t)st.size <= (size_t)r->page) {
+        std::memcpy(r->alias + (a - r->region), &st.value, (size_t)st.size);  // little-endian: the low bytes
+        retire_store(ctx, st);
+        ++r->emulated;
+        return;
+    }
     mprotect(r->region + (size_t)p * (size_t)r->page, (size_t)r->page, PROT_READ | PROT_WRITE);
+    ++r->protect_calls;
     if (f.dirty_hi < f.dirty_lo) {
         f.dirty_lo = p;
         f.dirty_hi = p;
@@ -285,11 +427,33 @@ int cdet_run(const cdet_run_cfg_t *cfg, cdet_run_result_t *res)
     r.npages = (cfg->counters + cfg->counters_per_page - 1) / cfg->counters_per_page;
     r.region_bytes = (size_t)r.npages * (size_t)r.page;
     r.detector = cfg->mode == CDET_DETECT || cfg->mode == CDET_ENFORCE;
-    void *m = mmap(nullptr, r.region_bytes, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    void *m = MAP_FAILED;
+    if (r.detector && cfg->emulate_stores) {
+        // one memory object mapped twice: the handlers' view (read-only
+        // while guarded) and the detector's writable alias
+        const int fd = memfd_create("cdet_region", MFD_CLOEXEC);
+        if (fd >= 0 && ftruncate(fd, (off_t)r.region_bytes) == 0) {
+            m = mmap(nullptr, r.region_bytes, PROT_READ | PROT_WRITE, MAP_SHARED, fd, 0);
+            void *al = m == MAP_FAILED ? MAP_FAILED
+                                       : mmap(nullptr, r.region_bytes, PROT_READ | PROT_WRITE, MAP_SHARED, fd, 0);
+            if (al == MAP_FAILED) {
+                if (m != MAP_FAILED)
+                    munmap(m, r.region_bytes);
+                m = MAP_FAILED;
+            } else {
+                r.alias = static_cast<uint8_t *>(al);
+            }
+        }
+        if (fd >= 0)
+            close(fd);
+    }
+    if (m == MAP_FAILED)
+        m = mmap(nullptr, r.region_bytes, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
     if (m == MAP_FAILED)
         return AES_ENOMEM;
     r.region = static_cast<uint8_t *>(m);
     r.page_version.assign((size_t)r.npages, 0);
+    r.page_writer.assign((size_t)r.npages, -1);
     r.fibers.resize((size_t)cfg->handlers);
     for (int i = 0; i < cfg->handlers; ++i) {
         Fiber &f = r.fibers[(size_t)i];
@@ -356,12 +520,129 @@ int cdet_run(const cdet_run_cfg_t *cfg, cdet_run_result_t *res)
         if (f.stack)
             munmap(f.stack, kStack);
     munmap(r.region, r.region_bytes);
+    if (r.alias)
+        munmap(r.alias, r.region_bytes);
     res->final_count = total;
     res->lost_updates = (uint64_t)cfg->requests - total;
     res->conflicts = r.conflicts;
     res->restarts = r.restarts;
     res->elapsed_s = elapsed;
+    res->emulated_stores = r.emulated;
+    res->protect_calls = r.protect_calls;
     return r.error;
+}
+
+int cdet_store_selftest(int rounds, uint64_t *emulated, uint64_t *fallbacks)
+{
+    if (rounds < 1 || !emulated || !fallbacks)
+        return AES_EINVAL;
+    if (g_run)
+        return AES_EINVAL;
+    Run r;
+    r.cfg = cdet_run_cfg_t{};
+    r.cfg.mode = CDET_DETECT;
+    r.page = sysconf(_SC_PAGESIZE);
+    r.npages = 2;
+    r.region_bytes = 2 * (size_t)r.page;
+    r.detector = true;
+    const int fd = memfd_create("cdet_selftest", MFD_CLOEXEC);
+    if (fd < 0)
+        return AES_ENOMEM;
+    void *m = MAP_FAILED, *al = MAP_FAILED;
+    if (ftruncate(fd, (off_t)r.region_bytes) == 0) {
+        m = mmap(nullptr, r.region_bytes, PROT_READ | PROT_WRITE, MAP_SHARED, fd, 0);
+        al = mmap(nullptr, r.region_bytes, PROT_READ | PROT_WRITE, MAP_SHARED, fd, 0);
+    }
+    close(fd);
+    if (m == MAP_FAILED || al == MAP_FAILED) {
+        if (m != MAP_FAILED)
+            munmap(m, r.region_bytes);
+        if (al != MAP_FAILED)
+            munmap(al, r.region_bytes);
+        return AES_ENOMEM;
+    }
+    r.region = static_cast<uint8_t *>(m);
+    r.alias = static_cast<uint8_t *>(al);
+    r.page_version.assign(2, 0);
+    r.page_writer.assign(2, -1);
+    r.fibers.resize(1);
+    r.current = &r.fibers[0];  // no park: every fault is a plain guarded write
+    std::vector<uint8_t> shadow(r.region_bytes, 0);
+    struct sigaction sa {};
+    sa.sa_sigaction = on_fault;
+    sa.sa_flags = SA_SIGINFO;
+    sigemptyset(&sa.sa_mask);
+    if (sigaction(SIGSEGV, &sa, &g_prev_segv) != 0) {
+        munmap(m, r.region_bytes);
+        munmap(al, r.region_bytes);
+        return AES_EINVAL;
+    }
+    g_run = &r;
+    // Stores of every width at run-time offsets (base + scaled index, with
+    // and without displacement), mirrored into a plain shadow copy; each
+    // round starts with the region read-only again.
+    volatile uint8_t *b8 = r.region;
+    volatile uint16_t *b16 = reinterpret_cast<volatile uint16_t *>(r.region);
+    volatile uint32_t *b32 = reinterpret_cast<volatile uint32_t *>(r.region);
+    volatile uint64_t *b64 = reinterpret_cast<volatile uint64_t *>(r.region);
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    const size_t n64 = r.region_bytes / 8;
+    for (int k = 0; k < rounds; ++k) {
+        mprotect(r.region, r.region_bytes, PROT_READ);
+        r.fibers[0].dirty_lo = 0;
+        r.fibers[0].dirty_hi = -1;
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        const size_t i = (size_t)(x % (n64 - 8));
+        const uint64_t v = x * 0xD6E8FEB86659FD93ull;
+        switch (k % 6) {
+        case 0:
+            b64[i] = v;
+            std::memcpy(&shadow[8 * i], &v, 8);
+            break;
+        case 1: {
+            const uint32_t w = (uint32_t)(v >> 7);
+            b32[2 * i + 1] = w;
+            std::memcpy(&shadow[8 * i + 4], &w, 4);
+            break;
+        }
+        case 2: {
+            const uint16_t h = (uint16_t)(v >> 21);
+            b16[4 * i + 3] = h;
+            std::memcpy(&shadow[8 * i + 6], &h, 2);
+            break;
+        }
+        case 3: {
+            const uint8_t c = (uint8_t)(v >> 40);
+            b8[8 * i + 5] = c;
+            shadow[8 * i + 5] = c;
+            break;
+        }
+        case 4:  // displacement past the index
+            b64[i + 7] = v ^ (uint64_t)k;
+            {
+                const uint64_t t = v ^ (uint64_t)k;
+                std::memcpy(&shadow[8 * (i + 7)], &t, 8);
+            }
+            break;
+        default: {  // a stored value that is the index itself
+            const uint64_t t = (uint64_t)i;
+            b64[i] = t;
+            std::memcpy(&shadow[8 * i], &t, 8);
+            break;
+        }
+        }
+    }
+    sigaction(SIGSEGV, &g_prev_segv, nullptr);
+    g_run = nullptr;
+    mprotect(r.region, r.region_bytes, PROT_READ | PROT_WRITE);
+    const bool same = std::memcmp(r.region, shadow.data(), r.region_bytes) == 0;
+    *emulated = r.emulated;
+    *fallbacks = r.protect_calls;
+    munmap(m, r.region_bytes);
+    munmap(al, r.region_bytes);
+    return same ? AES_OK : AES_EDESC;
 }
 
 }  // extern "C"

@@ -106,3 +106,43 @@ def test_pattern_arguments():
         A.conflict_run(A.CDET_DETECT, pattern=4)
     with pytest.raises(A.AesError):  # per-connection needs a counter per handler
         A.conflict_run(A.CDET_DETECT, handlers=16, counters=8, pattern=A.CDET_PATTERN_PER_CONN)
+
+
+def test_store_emulation_selftest():
+    """Guarded stores of 8..64 bits at run-time offsets, performed by the
+    fault handler, leave the region equal to a plain shadow copy; on x86-64
+    and AArch64 the compiler's plain stores are all decoded."""
+    import platform
+
+    r = A.store_selftest(6000)
+    assert r["emulated"] + r["fallbacks"] == 6000
+    if platform.machine() in ("x86_64", "aarch64"):
+        assert r["emulated"] == 6000 and r["fallbacks"] == 0, r
+
+
+@pytest.mark.parametrize("mode", [A.CDET_DETECT, A.CDET_ENFORCE], ids=["detect", "enforce"])
+def test_emulated_stores_keep_the_detectors_results(mode):
+    """With store emulation the guarded pages never change protection and the
+    detector reports what it reports without it: enforcement loses nothing,
+    detection flags at least every lost update, safe patterns stay silent."""
+    r = A.conflict_run(mode, handlers=16, requests=N, counters=64, emulate_stores=True)
+    assert r["protect_calls"] == 0 and r["emulated_stores"] >= N, r
+    if mode == A.CDET_ENFORCE:
+        assert r["lost_updates"] == 0 and r["final_count"] == N and r["restarts"] == r["conflicts"] > 0
+    else:
+        assert r["lost_updates"] > 0 and r["conflicts"] >= r["lost_updates"]
+    for pattern in (A.CDET_PATTERN_READONLY, A.CDET_PATTERN_PER_CONN, A.CDET_PATTERN_LOCKED):
+        s = A.conflict_run(mode, handlers=16, requests=1000, counters=64, pattern=pattern, emulate_stores=True)
+        assert s["conflicts"] == 0 and s["lost_updates"] == 0, (pattern, s)
+
+
+def test_protection_changes_per_guarded_write():
+    """One handler, no offload: each request's guarded write costs two
+    protection changes (unprotect at the fault, protect again after the
+    request), and none with store emulation."""
+    n = 2000
+    plain = A.conflict_run(A.CDET_DETECT, 1, n, 1, offload_ns=0)
+    emu = A.conflict_run(A.CDET_DETECT, 1, n, 1, offload_ns=0, emulate_stores=True)
+    assert plain["final_count"] == n and emu["final_count"] == n
+    assert plain["protect_calls"] == 2 * n and plain["emulated_stores"] == 0
+    assert emu["protect_calls"] == 0 and emu["emulated_stores"] == n
