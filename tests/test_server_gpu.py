@@ -244,13 +244,23 @@ def test_light_load_keeps_every_cta_resident(cuda, aes, ncpu):
         n, size = 60, 1024
         payload, offs, src, dst = arena(cuda, g, [size] * n)
         ivs = [W.random_bytes(g, 16) for _ in range(n)]
-        t_start, base = time.time(), None
+        # Start from a launch whose CTAs are all resident: if the setup above
+        # outlasted the idle timeout, let that launch end and relaunch it.
+        t = srv.submit(slot, ivs[0].tobytes(), src.data_ptr() + int(offs[0]), dst.data_ptr() + int(offs[0]), size)
+        assert srv.wait(t, WAIT_US) == aes.AES_OK
+        if srv.stats()["kernel_status"] != 0:
+            deadline = time.time() + 5
+            while srv.stats()["running"] and time.time() < deadline:
+                time.sleep(0.01)
+            t = srv.submit(slot, ivs[0].tobytes(), src.data_ptr() + int(offs[0]), dst.data_ptr() + int(offs[0]),
+                           size)
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+        base = srv.stats()["relaunches"]
+        t_start = time.time()
         for i in range(n):
             o = int(offs[i])
             t = srv.submit(slot, ivs[i].tobytes(), src.data_ptr() + o, dst.data_ptr() + o, size)
             assert srv.wait(t, WAIT_US) == aes.AES_OK
-            if base is None:  # the setup above may have outlasted the idle timeout
-                base = srv.stats()["relaunches"]
             time.sleep(0.01)
         elapsed = time.time() - t_start
         st = srv.stats()
