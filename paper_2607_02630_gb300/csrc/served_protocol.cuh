@@ -329,20 +329,31 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
         rec->tile_groups = tg;
         rec->tile_parts = tp;
         ent[i] = ring_entry(k, d, ntiles);
+        if (PER_REQ)  // with the record: a claim that sees the claim word below finds it
+            st_relaxed_gpu(&rec->seq_ntiles, ((uint64_t)k << kTileBits) | ntiles);
         if (ntiles == 0)
             done_word[i] = ok ? 1u : 2u;
     }
     fence_gpu();
+    if (PER_REQ) {
+        // One fence: the claim word and the ring entry follow the record.  A
+        // claimer that sees the ring entry before the claim word retries
+        // (it reads an older sequence number there).
 #pragma unroll
-    for (uint32_t i = 0; i < kDispatchBatch; ++i) {
-        const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
-        if (i < m && d != 0xffffu) {
-            st_relaxed_gpu(&p.recs[d].seq_ntiles, ((ent[i] >> 36) << kTileBits) | (ent[i] & kTileMask));
-            if (PER_REQ)
+        for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+            const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
+            if (i < m && d != 0xffffu)
                 st_relaxed_gpu(&p.recs[d].claim, (ent[i] >> 36) << kClaimShift);
         }
+    } else {
+#pragma unroll
+        for (uint32_t i = 0; i < kDispatchBatch; ++i) {
+            const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
+            if (i < m && d != 0xffffu)
+                st_relaxed_gpu(&p.recs[d].seq_ntiles, ((ent[i] >> 36) << kTileBits) | (ent[i] & kTileMask));
+        }
+        fence_gpu();
     }
-    fence_gpu();
 #pragma unroll
     for (uint32_t i = 0; i < kDispatchBatch; ++i)
         if (i < m)
