@@ -594,9 +594,9 @@ int cdet_store_selftest(int rounds, uint64_t *emulated, uint64_t *fallbacks)
         x ^= x << 13;
         x ^= x >> 7;
         x ^= x << 17;
-        const size_t i = (size_t)(x % (n64 - 8));
+        const size_t i = (size_t)(x % (n64 - 320));
         const uint64_t v = x * 0xD6E8FEB86659FD93ull;
-        switch (k % 6) {
+        switch (k % 7) {
         case 0:
             b64[i] = v;
             std::memcpy(&shadow[8 * i], &v, 8);
@@ -626,6 +626,12 @@ int cdet_store_selftest(int rounds, uint64_t *emulated, uint64_t *fallbacks)
                 std::memcpy(&shadow[8 * (i + 7)], &t, 8);
             }
             break;
+        case 5: {  // a displacement beyond 8 bits (2560 bytes past the index)
+            const uint64_t t = ~v;
+            b64[i + 319] = t;
+            std::memcpy(&shadow[8 * (i + 319)], &t, 8);
+            break;
+        }
         default: {  // a stored value that is the index itself
             const uint64_t t = (uint64_t)i;
             b64[i] = t;
