@@ -153,6 +153,10 @@ SRV_INLINE unsigned long long atom_cas(unsigned long long *p, unsigned long long
 }
 SRV_INLINE unsigned long long atom_exch(unsigned long long *p, unsigned long long v) { return atomicExch(p, v); }
 #else
+// Host build: loads acquire, stores release, read-modify-writes acq_rel.
+// Stronger than the device's relaxed operations plus fences: the host runs
+// check the protocol's logic, not its memory ordering (a thread sanitizer,
+// which does not model fences, then reports no false races).
 inline uint64_t gtime()
 {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -160,14 +164,14 @@ inline uint64_t gtime()
 }
 inline void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
 {
-    a = __atomic_load_n(p, __ATOMIC_RELAXED);
-    b = __atomic_load_n(p + 1, __ATOMIC_RELAXED);
+    a = __atomic_load_n(p, __ATOMIC_ACQUIRE);
+    b = __atomic_load_n(p + 1, __ATOMIC_ACQUIRE);
 }
-inline uint64_t ld_relaxed_gpu(const unsigned long long *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
-inline void st_relaxed_gpu(unsigned long long *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELAXED); }
+inline uint64_t ld_relaxed_gpu(const unsigned long long *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+inline void st_relaxed_gpu(unsigned long long *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
 inline void st_release_sys(unsigned long long *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
-inline uint32_t ld_volatile(const unsigned int *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
-inline uint64_t ld_relaxed_sys(const uint64_t *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
+inline uint32_t ld_volatile(const unsigned int *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+inline uint64_t ld_relaxed_sys(const uint64_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 inline void fence_acq_rel_sys() { __atomic_thread_fence(__ATOMIC_ACQ_REL); }
 inline void fence_gpu() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
 inline void fence_sys() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
@@ -175,21 +179,21 @@ inline void nap(unsigned) { std::this_thread::yield(); }
 template <class T>
 inline T ld_cg(const T *p)
 {
-    return __atomic_load_n(p, __ATOMIC_RELAXED);
+    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
 }
 inline unsigned long long atom_add(unsigned long long *p, unsigned long long v)
 {
-    return __atomic_fetch_add(p, v, __ATOMIC_RELAXED);
+    return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL);
 }
-inline unsigned int atom_add(unsigned int *p, unsigned int v) { return __atomic_fetch_add(p, v, __ATOMIC_RELAXED); }
+inline unsigned int atom_add(unsigned int *p, unsigned int v) { return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL); }
 inline unsigned long long atom_cas(unsigned long long *p, unsigned long long c, unsigned long long v)
 {
-    __atomic_compare_exchange_n(p, &c, v, false, __ATOMIC_RELAXED, __ATOMIC_RELAXED);
+    __atomic_compare_exchange_n(p, &c, v, false, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE);
     return c;
 }
 inline unsigned long long atom_exch(unsigned long long *p, unsigned long long v)
 {
-    return __atomic_exchange_n(p, v, __ATOMIC_RELAXED);
+    return __atomic_exchange_n(p, v, __ATOMIC_ACQ_REL);
 }
 #endif
 
