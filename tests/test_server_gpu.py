@@ -16,7 +16,7 @@ import pytest
 import oracle
 from paper_2607_02630_gb300 import workloads as W
 
-from gpu_util import iv_plus, to_dev, to_host
+from gpu_util import iv_plus, iv_with_low, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -579,5 +579,35 @@ def test_server_shapes_match_oracle(cuda, aes, ncpu, cfg):
             key, bits = keys[i % 3]
             np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, bits, ivs[i], payload[o: o + n], ncpu))
             assert (out[o + n: o + n + 16] == 0xA5).all()
+    finally:
+        assert srv.close() == aes.AES_OK
+
+
+@pytest.mark.parametrize("cfg", [{}, {"tile_blocks": 64}, {"tile_blocks": 1024}], ids=["per_request", "t64", "t1024"])
+def test_served_counter_carries_match_oracle(cuda, aes, ncpu, cfg):
+    """Initial counters 8 blocks below a carry out of the low 32 and 64 bits
+    and below the 2^128 wrap: every served request's bytes match the
+    oracle's full 128-bit counter (SP 800-38A App. B.1, m = 128)."""
+    srv = aes.Server(slots=32, max_keys=2, idle_timeout_us=500_000, **cfg)
+    try:
+        g = W.rng(69)
+        keys = [(W.random_bytes(g, 16), 128), (W.random_bytes(g, 32), 256)]
+        slots = [srv.key_register(k.tobytes(), b) for k, b in keys]
+        sizes = [100, 129, 4096 + 5, 65536 + 7, (1 << 20) + 9]
+        kinds = ["low32", "low64", "wrap128"]
+        cases = [(n, kind, j % 2) for j, (n, kind) in enumerate((n, k) for n in sizes for k in kinds)]
+        payload, offs, src, dst = arena(cuda, g, [n for n, _, _ in cases])
+        tickets = []
+        for i, (n, kind, k) in enumerate(cases):
+            iv = iv_with_low(g, kind)
+            o = int(offs[i])
+            t = srv.submit(slots[k], iv.tobytes(), src.data_ptr() + o, dst.data_ptr() + o, n)
+            tickets.append((t, iv, o, n, k))
+        for t, *_ in tickets:
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+        out = to_host(dst)
+        for t, iv, o, n, k in tickets:
+            key, bits = keys[k]
+            np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, bits, iv, payload[o: o + n], ncpu))
     finally:
         assert srv.close() == aes.AES_OK
