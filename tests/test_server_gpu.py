@@ -611,3 +611,26 @@ def test_served_counter_carries_match_oracle(cuda, aes, ncpu, cfg):
             np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, bits, iv, payload[o: o + n], ncpu))
     finally:
         assert srv.close() == aes.AES_OK
+
+
+def test_served_in_place_matches_oracle(cuda, aes, ncpu):
+    """Served requests that encrypt in place (in == out) give the oracle's
+    bytes."""
+    srv = aes.Server(slots=16, max_keys=1, idle_timeout_us=500_000)
+    try:
+        g = W.rng(70)
+        key = W.random_bytes(g, 32)
+        slot = srv.key_register(key.tobytes(), 256)
+        sizes = [1, 16, 4096 + 3, (1 << 20) + 5, 3 << 20]
+        payload, offs, src, _ = arena(cuda, g, sizes)
+        ivs = [W.random_bytes(g, 16) for _ in sizes]
+        tickets = [srv.submit(slot, ivs[i].tobytes(), src.data_ptr() + int(offs[i]), src.data_ptr() + int(offs[i]),
+                              n) for i, n in enumerate(sizes)]
+        for t in tickets:
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+        out = to_host(src)
+        for i, n in enumerate(sizes):
+            o = int(offs[i])
+            np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, 256, ivs[i], payload[o: o + n], ncpu))
+    finally:
+        assert srv.close() == aes.AES_OK
