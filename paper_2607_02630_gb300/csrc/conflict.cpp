@@ -134,7 +134,8 @@ void protect_dirty(Run &r, Fiber &f)
 // is the expensive part in a process that shares its page tables with a GPU.
 // Decoded are the plain general-register stores a compiler emits for an
 // aggregate update:
-//   x86-64: MOV r/m8|16|32|64, r (opcodes 88 / 89, optional 66 and REX);
+//   x86-64: MOV r/m8|16|32|64, r and MOV r/m, imm (opcodes 88 / 89 and
+//   C6 / C7 with ModRM.reg 0; optional 66 and REX prefixes);
 //   AArch64: STR / STUR / STTR of 8..64-bit general registers (immediate
 //   unsigned offset, unscaled, pre- and post-index with base write-back,
 //   register offset).
@@ -170,12 +171,14 @@ bool decode_store(const ucontext_t *uc, Store *st)
     if ((ip[i] & 0xF0) == 0x40)
         rex = ip[i++];
     const uint8_t op = ip[i++];
-    if (op != 0x88 && op != 0x89)
+    if (op != 0x88 && op != 0x89 && op != 0xC6 && op != 0xC7)
         return false;
     const uint8_t modrm = ip[i++];
     const int mod = modrm >> 6, rm = modrm & 7, reg = (modrm >> 3) & 7;
     if (mod == 3)
         return false;  // register destination: not a store
+    if ((op == 0xC6 || op == 0xC7) && reg != 0)
+        return false;  // C6 / C7 with another ModRM.reg are not MOV
     if (rm == 4) {     // SIB byte; base 101 with mod 00 means disp32 and no base
         const uint8_t sib = ip[i++];
         if (mod == 0 && (sib & 7) == 5)
@@ -187,7 +190,20 @@ bool decode_store(const ucontext_t *uc, Store *st)
         i += 1;
     else if (mod == 2)
         i += 4;
-    if (op == 0x88) {
+    if (op == 0xC6 || op == 0xC7) {  // the immediate follows the address bytes
+        st->size = op == 0xC6 ? 1 : ((rex & 8) ? 8 : (op16 ? 2 : 4));
+        const int isz = st->size == 8 ? 4 : st->size;  // imm32, sign-extended for 64-bit stores
+        int64_t imm = 0;
+        if (isz == 1)
+            imm = (int8_t)ip[i];
+        else if (isz == 2)
+            imm = (int16_t)(ip[i] | (ip[i + 1] << 8));
+        else
+            imm = (int32_t)((uint32_t)ip[i] | ((uint32_t)ip[i + 1] << 8) | ((uint32_t)ip[i + 2] << 16) |
+                            ((uint32_t)ip[i + 3] << 24));
+        i += isz;
+        st->value = (uint64_t)imm;
+    } else if (op == 0x88) {
         st->size = 1;
         if (!rex && reg >= 4)  // AH, CH, DH, BH
             st->value = (uint64_t)g[x86_greg(reg - 4)] >> 8;
@@ -596,7 +612,23 @@ int cdet_store_selftest(int rounds, uint64_t *emulated, uint64_t *fallbacks)
         x ^= x << 17;
         const size_t i = (size_t)(x % (n64 - 320));
         const uint64_t v = x * 0xD6E8FEB86659FD93ull;
-        switch (k % 7) {
+        switch (k % 10) {
+        case 6: {  // constants: stored from an immediate on x86-64
+            b64[i] = 0x5A5A1234ull;
+            const uint64_t t = 0x5A5A1234ull;
+            std::memcpy(&shadow[8 * i], &t, 8);
+            break;
+        }
+        case 7: {
+            b16[4 * i + 1] = 0xBEEF;
+            const uint16_t h = 0xBEEF;
+            std::memcpy(&shadow[8 * i + 2], &h, 2);
+            break;
+        }
+        case 8:
+            b8[8 * i + 7] = 0x7F;
+            shadow[8 * i + 7] = 0x7F;
+            break;
         case 0:
             b64[i] = v;
             std::memcpy(&shadow[8 * i], &v, 8);
