@@ -315,7 +315,9 @@ int offload_server_stats(offload_server_t srv, offload_stats_t *out);
 /* Raise the stop flag, wait (bounded, 5 s) for the resident kernel to exit,
  * and free everything.  Requests still in flight are abandoned.  Returns
  * AES_ETIMEOUT if the kernel did not exit in time (resources are then leaked
- * rather than freed under a running kernel). */
+ * rather than freed under a running kernel).  The frees (cudaFree,
+ * cudaFreeHost) wait for the device's work in flight, so with other servers
+ * resident this returns after their next idle exit. */
 int offload_server_destroy(offload_server_t srv);
 
 /* ------------------------------------------------------------ load drivers */
