@@ -157,6 +157,26 @@ SRV_INLINE unsigned long long atom_exch(unsigned long long *p, unsigned long lon
 // Stronger than the device's relaxed operations plus fences: the host runs
 // check the protocol's logic, not its memory ordering (a thread sanitizer,
 // which does not model fences, then reports no false races).
+// Schedule perturbation for host runs: with chaos_period() = n > 0, each
+// protocol memory operation yields the thread with probability 1/n, so host
+// threads meet the protocol's steps in far more interleavings.
+inline int &chaos_period()
+{
+    static int n = 0;
+    return n;
+}
+inline void chaos()
+{
+    const int n = chaos_period();
+    if (n <= 0)
+        return;
+    thread_local uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)(uintptr_t)&x;
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    if (x % (uint64_t)n == 0)
+        std::this_thread::yield();
+}
 inline uint64_t gtime()
 {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -164,14 +184,31 @@ inline uint64_t gtime()
 }
 inline void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
 {
+    chaos();
     a = __atomic_load_n(p, __ATOMIC_ACQUIRE);
     b = __atomic_load_n(p + 1, __ATOMIC_ACQUIRE);
 }
-inline uint64_t ld_relaxed_gpu(const unsigned long long *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
-inline void st_relaxed_gpu(unsigned long long *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
-inline void st_release_sys(unsigned long long *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+inline uint64_t ld_relaxed_gpu(const unsigned long long *p)
+{
+    chaos();
+    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
+}
+inline void st_relaxed_gpu(unsigned long long *p, uint64_t v)
+{
+    chaos();
+    __atomic_store_n(p, v, __ATOMIC_RELEASE);
+}
+inline void st_release_sys(unsigned long long *p, uint64_t v)
+{
+    chaos();
+    __atomic_store_n(p, v, __ATOMIC_RELEASE);
+}
 inline uint32_t ld_volatile(const unsigned int *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
-inline uint64_t ld_relaxed_sys(const uint64_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+inline uint64_t ld_relaxed_sys(const uint64_t *p)
+{
+    chaos();
+    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
+}
 inline void fence_acq_rel_sys() { __atomic_thread_fence(__ATOMIC_ACQ_REL); }
 inline void fence_gpu() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
 inline void fence_sys() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
@@ -183,16 +220,23 @@ inline T ld_cg(const T *p)
 }
 inline unsigned long long atom_add(unsigned long long *p, unsigned long long v)
 {
+    chaos();
     return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL);
 }
-inline unsigned int atom_add(unsigned int *p, unsigned int v) { return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL); }
+inline unsigned int atom_add(unsigned int *p, unsigned int v)
+{
+    chaos();
+    return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL);
+}
 inline unsigned long long atom_cas(unsigned long long *p, unsigned long long c, unsigned long long v)
 {
+    chaos();
     __atomic_compare_exchange_n(p, &c, v, false, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE);
     return c;
 }
 inline unsigned long long atom_exch(unsigned long long *p, unsigned long long v)
 {
+    chaos();
     return __atomic_exchange_n(p, v, __ATOMIC_ACQ_REL);
 }
 #endif

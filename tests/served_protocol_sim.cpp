@@ -12,7 +12,8 @@
 // issues (the CTAs must stop with ERROR).  Logic only: host memory ordering
 // is not the GPU's.
 //
-// usage: served_protocol_sim mode ctas slots requests tile_blocks idle_us seed [scenario]
+// usage: served_protocol_sim mode ctas slots requests tile_blocks idle_us seed [scenario [chaos]]
+// (chaos n > 0: every protocol memory operation yields with probability 1/n)
 #include "served_protocol.cuh"
 
 #include <atomic>
@@ -448,8 +449,9 @@ struct Sim {
 
 int main(int argc, char **argv)
 {
-    if (argc != 8 && argc != 9) {
-        std::fprintf(stderr, "usage: %s mode ctas slots requests tile_blocks idle_us seed [scenario]\n", argv[0]);
+    if (argc < 8 || argc > 10) {
+        std::fprintf(stderr, "usage: %s mode ctas slots requests tile_blocks idle_us seed [scenario [chaos]]\n",
+                     argv[0]);
         return 2;
     }
     Sim s;
@@ -460,6 +462,7 @@ int main(int argc, char **argv)
     s.tile_blocks = std::atoi(argv[5]);
     s.idle_ns = 1000ull * (uint64_t)std::atoll(argv[6]);
     s.seed = (uint32_t)std::atoi(argv[7]);
-    s.scenario = argc == 9 ? std::atoi(argv[8]) : 0;
+    s.scenario = argc >= 9 ? std::atoi(argv[8]) : 0;
+    srvp::chaos_period() = argc >= 10 ? std::atoi(argv[9]) : 0;
     return s.run();
 }

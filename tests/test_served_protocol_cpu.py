@@ -68,3 +68,22 @@ def test_invalid_queue_entry_stops_with_error(sim, mode):
                        timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
     assert "status=" in r.stdout and int(r.stdout.split("status=")[1].split()[0]) & 4
+
+
+# ctas, slots, requests, tile_blocks, idle us, seed, scenario, chaos period
+CHAOS = [
+    (8, 4, 1500, 0, 2000, 52, 0, 2),
+    (4, 1, 600, 64, 2000, 61, 0, 3),
+    (12, 16, 2000, 0, 500, 62, 0, 4),
+    (4, 16, 1000, 0, 5000, 63, 1, 3),
+]
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["global_cursor", "per_request"])
+@pytest.mark.parametrize("case", CHAOS, ids=[f"c{c[0]}s{c[1]}sc{c[6]}ch{c[7]}" for c in CHAOS])
+def test_under_schedule_perturbation(sim, mode, case):
+    """The same checks with every protocol memory operation yielding the
+    thread at random (1 in `chaos`), so the steps of different CTAs and the
+    producer interleave far more finely."""
+    r = subprocess.run([sim, str(mode)] + [str(x) for x in case], capture_output=True, text=True, timeout=240)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
