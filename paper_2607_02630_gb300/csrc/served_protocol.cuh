@@ -22,8 +22,11 @@
 #define SRV_NOINLINE __device__ __noinline__
 #define SRV_FN __device__
 #else
+#include <atomic>
 #include <chrono>
+#include <cstring>
 #include <thread>
+#include <vector>
 #define SRV_INLINE inline
 #define SRV_NOINLINE inline
 #define SRV_FN inline
@@ -59,8 +62,8 @@ constexpr uint32_t kClaimShift = 36;
 constexpr uint64_t kClaimTileMask = (1ull << kClaimShift) - 1;
 constexpr uint64_t kDispBusy = 1ull << 40;
 
-struct QEntry {  // 64 bytes, host-written, tag last
-    uint64_t tag;  // sequence number + 1
+struct QEntry {  // 64 bytes, host-written into the request's slot before its order word
+    uint64_t tag;  // sequence number + 1 (informational)
     uint64_t in, out, len, iv_hi, iv_lo, gen;
     uint32_t key_slot;
     uint16_t desc;   // slot index d
@@ -91,7 +94,8 @@ struct SrvParams {
     SrvRec *recs;
     const uint4 *keys;          // max_keys x 15 round keys
     const int *key_nr;          // max_keys; 0 = unregistered
-    const QEntry *queue;        // mapped
+    const QEntry *queue;        // mapped: the body of the request in slot d at queue[d]
+    const uint64_t *order;      // mapped: order[s & qmask] = ((s + 1) << 16) | d, stored after the body
     unsigned long long *done;   // mapped
     const unsigned int *stop;   // mapped
     unsigned int *kstatus;      // mapped
@@ -153,29 +157,125 @@ SRV_INLINE unsigned long long atom_cas(unsigned long long *p, unsigned long long
 }
 SRV_INLINE unsigned long long atom_exch(unsigned long long *p, unsigned long long v) { return atomicExch(p, v); }
 #else
-// Host build: loads acquire, stores release, read-modify-writes acq_rel.
-// Stronger than the device's relaxed operations plus fences: the host runs
-// check the protocol's logic, not its memory ordering (a thread sanitizer,
-// which does not model fences, then reports no false races).
-// Schedule perturbation for host runs: with chaos_period() = n > 0, each
-// protocol memory operation yields the thread with probability 1/n, so host
-// threads meet the protocol's steps in far more interleavings.
+// Host build, for threads that stand in for CTAs.  By default loads
+// acquire, stores release and read-modify-writes are acq_rel: stronger than
+// the device's relaxed operations plus fences, so a run checks the
+// protocol's logic (and a thread sanitizer, which does not model fences,
+// reports no false races).  Two switches make runs harsher:
+//  * chaos_period() = n > 0: each protocol memory operation yields the
+//    thread with probability 1/n, for finer interleavings;
+//  * weak_stores() = true: stores wait in a per-thread buffer and become
+//    visible later and out of order (per address in program order), all at
+//    once at the thread's next fence, release store or wait, and one at a
+//    time with probability 1/2 at each store and load.  A thread's loads see
+//    its own buffered stores first; a read-modify-write first makes the
+//    thread's buffered stores to its address visible.  This is closer to the
+//    device's relaxed stores than any CPU, so fence placement is exercised.
 inline int &chaos_period()
 {
     static int n = 0;
     return n;
 }
-inline void chaos()
+inline bool &weak_stores()
 {
-    const int n = chaos_period();
-    if (n <= 0)
-        return;
+    static bool w = false;
+    return w;
+}
+inline uint64_t host_rand()
+{
     thread_local uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)(uintptr_t)&x;
     x ^= x << 13;
     x ^= x >> 7;
     x ^= x << 17;
-    if (x % (uint64_t)n == 0)
+    return x;
+}
+inline void chaos()
+{
+    const int n = chaos_period();
+    if (n > 0 && host_rand() % (uint64_t)n == 0)
         std::this_thread::yield();
+}
+struct PendingStore {
+    void *p;
+    uint64_t v;
+    int size;
+};
+inline std::vector<PendingStore> &store_buf()
+{
+    thread_local std::vector<PendingStore> b;
+    return b;
+}
+inline void put(const PendingStore &s)
+{
+    switch (s.size) {
+    case 1: __atomic_store_n(static_cast<uint8_t *>(s.p), (uint8_t)s.v, __ATOMIC_RELEASE); break;
+    case 2: __atomic_store_n(static_cast<uint16_t *>(s.p), (uint16_t)s.v, __ATOMIC_RELEASE); break;
+    case 4: __atomic_store_n(static_cast<uint32_t *>(s.p), (uint32_t)s.v, __ATOMIC_RELEASE); break;
+    default: __atomic_store_n(static_cast<uint64_t *>(s.p), s.v, __ATOMIC_RELEASE); break;
+    }
+}
+// every buffered store of this thread becomes visible (fence, release, exit)
+inline void drain_stores()
+{
+    auto &b = store_buf();
+    for (const auto &s : b)
+        put(s);
+    b.clear();
+}
+inline void drain_address(const void *p)
+{
+    auto &b = store_buf();
+    size_t w = 0;
+    for (size_t i = 0; i < b.size(); ++i) {
+        if (b[i].p == p)
+            put(b[i]);
+        else
+            b[w++] = b[i];
+    }
+    b.resize(w);
+}
+inline void drain_one_maybe()
+{
+    auto &b = store_buf();
+    if (b.empty() || (host_rand() & 1))
+        return;
+    size_t i = (size_t)(host_rand() % b.size());
+    for (size_t j = 0; j < i; ++j)  // per address, program order
+        if (b[j].p == b[i].p) {
+            i = j;
+            break;
+        }
+    put(b[i]);
+    b.erase(b.begin() + (std::ptrdiff_t)i);
+}
+template <class T>
+inline void st_weak(T *p, T v)
+{
+    chaos();
+    if (!weak_stores()) {
+        __atomic_store_n(p, v, __ATOMIC_RELEASE);
+        return;
+    }
+    uint64_t u = 0;
+    std::memcpy(&u, &v, sizeof(T));
+    store_buf().push_back(PendingStore{(void *)p, u, (int)sizeof(T)});
+    drain_one_maybe();
+}
+template <class T>
+inline T ld_weak(const T *p)
+{
+    chaos();
+    if (weak_stores()) {
+        const auto &b = store_buf();
+        for (size_t i = b.size(); i-- > 0;)
+            if (b[i].p == p) {
+                T v;
+                std::memcpy(&v, &b[i].v, sizeof(T));
+                return v;
+            }
+        drain_one_maybe();
+    }
+    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
 }
 inline uint64_t gtime()
 {
@@ -184,61 +284,95 @@ inline uint64_t gtime()
 }
 inline void ld_volatile_v2(const uint64_t *p, uint64_t &a, uint64_t &b)
 {
-    chaos();
-    a = __atomic_load_n(p, __ATOMIC_ACQUIRE);
-    b = __atomic_load_n(p + 1, __ATOMIC_ACQUIRE);
+    a = ld_weak(p);
+    b = ld_weak(p + 1);
 }
-inline uint64_t ld_relaxed_gpu(const unsigned long long *p)
-{
-    chaos();
-    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
-}
-inline void st_relaxed_gpu(unsigned long long *p, uint64_t v)
-{
-    chaos();
-    __atomic_store_n(p, v, __ATOMIC_RELEASE);
-}
+inline uint64_t ld_relaxed_gpu(const unsigned long long *p) { return ld_weak(p); }
+inline void st_relaxed_gpu(unsigned long long *p, uint64_t v) { st_weak(p, (unsigned long long)v); }
 inline void st_release_sys(unsigned long long *p, uint64_t v)
 {
     chaos();
+    drain_stores();
     __atomic_store_n(p, v, __ATOMIC_RELEASE);
 }
-inline uint32_t ld_volatile(const unsigned int *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
-inline uint64_t ld_relaxed_sys(const uint64_t *p)
+inline uint32_t ld_volatile(const unsigned int *p) { return ld_weak(p); }
+inline uint64_t ld_relaxed_sys(const uint64_t *p) { return ld_weak(p); }
+inline void fence_acq_rel_sys()
 {
-    chaos();
-    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
+    drain_stores();
+    __atomic_thread_fence(__ATOMIC_ACQ_REL);
 }
-inline void fence_acq_rel_sys() { __atomic_thread_fence(__ATOMIC_ACQ_REL); }
-inline void fence_gpu() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
-inline void fence_sys() { __atomic_thread_fence(__ATOMIC_SEQ_CST); }
-inline void nap(unsigned) { std::this_thread::yield(); }
+inline void fence_gpu()
+{
+    drain_stores();
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+}
+inline void fence_sys()
+{
+    drain_stores();
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+}
+inline void nap(unsigned)
+{
+    drain_stores();  // a waiting thread's stores reach memory (forward progress)
+    std::this_thread::yield();
+}
 template <class T>
 inline T ld_cg(const T *p)
 {
-    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
+    return ld_weak(p);
 }
 inline unsigned long long atom_add(unsigned long long *p, unsigned long long v)
 {
     chaos();
+    drain_address(p);
     return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL);
 }
 inline unsigned int atom_add(unsigned int *p, unsigned int v)
 {
     chaos();
+    drain_address(p);
     return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL);
 }
 inline unsigned long long atom_cas(unsigned long long *p, unsigned long long c, unsigned long long v)
 {
     chaos();
+    drain_address(p);
     __atomic_compare_exchange_n(p, &c, v, false, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE);
     return c;
 }
 inline unsigned long long atom_exch(unsigned long long *p, unsigned long long v)
 {
     chaos();
+    drain_address(p);
     return __atomic_exchange_n(p, v, __ATOMIC_ACQ_REL);
 }
+#endif
+
+// A plain store to a record field (on the host, a weak store).
+#ifdef __CUDACC__
+template <class T>
+SRV_INLINE void st_field(T *p, T v)
+{
+    *p = v;
+}
+#define SRV_STAT(field) ((void)0)
+#else
+template <class T>
+inline void st_field(T *p, T v)
+{
+    st_weak(p, v);
+}
+// How often host runs take the protocol's rare paths.
+struct HostStats {
+    std::atomic<uint64_t> stale_claim_retries{0}, recycled_claims{0}, low_repairs{0};
+};
+inline HostStats &host_stats()
+{
+    static HostStats s;
+    return s;
+}
+#define SRV_STAT(field) (::srvp::host_stats().field.fetch_add(1, std::memory_order_relaxed))
 #endif
 
 // Nanoseconds since t0, as a signed count: a timer that steps back reads as
@@ -287,17 +421,18 @@ SRV_INLINE uint64_t ring_entry(uint32_t k, uint32_t d, uint32_t ntiles)
 template <bool PER_REQ>
 SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, uint64_t *first = nullptr)
 {
+    // The order words name each request's slot; its body sits in the slot,
+    // which the request holds until it completes, so the body cannot change
+    // between these reads and the body reads below, however long they take.
     uint32_t m = 0;
-    {
-        uint64_t tag[kDispatchBatch];
+    uint64_t ow[kDispatchBatch];
 #pragma unroll
-        for (uint32_t i = 0; i < kDispatchBatch; ++i)
-            tag[i] = i < n_max ? ld_relaxed_sys(&p.queue[(k0 + i) & p.qmask].tag) : 0;
+    for (uint32_t i = 0; i < kDispatchBatch; ++i)
+        ow[i] = i < n_max ? ld_relaxed_sys(p.order + ((k0 + i) & p.qmask)) : 0;
 #pragma unroll
-        for (uint32_t i = 0; i < kDispatchBatch; ++i)
-            if (m == i && i < n_max && (uint32_t)(tag[i] & kSeqMask) == ((k0 + i + 1) & kSeqMask))
-                m = i + 1;
-    }
+    for (uint32_t i = 0; i < kDispatchBatch; ++i)
+        if (m == i && i < n_max && (uint32_t)((ow[i] >> 16) & kSeqMask) == ((k0 + i + 1) & kSeqMask))
+            m = i + 1;
     if (m == 0)
         return 0;
     fence_acq_rel_sys();
@@ -306,8 +441,8 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
     uint64_t x[kDispatchBatch][7];
 #pragma unroll
     for (uint32_t i = 0; i < kDispatchBatch; ++i) {
-        if (i < m) {
-            const uint64_t *e = reinterpret_cast<const uint64_t *>(p.queue + ((k0 + i) & p.qmask));
+        if (i < m && (uint32_t)(ow[i] & 0xffffu) < p.nslots) {
+            const uint64_t *e = reinterpret_cast<const uint64_t *>(p.queue + (ow[i] & 0xffffu));
             uint64_t unused;
             ld_volatile_v2(e + 0, unused, x[i][0]);
             ld_volatile_v2(e + 2, x[i][1], x[i][2]);
@@ -325,7 +460,7 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
         const uint32_t k = (k0 + i) & kSeqMask;
         const uint64_t in = x[i][0], out = x[i][1], len = x[i][2], iv_hi = x[i][3], iv_lo = x[i][4];
         const uint32_t ks = (uint32_t)x[i][6];
-        const uint32_t d = (uint32_t)(x[i][6] >> 32) & 0xffffu;
+        const uint32_t d = (uint32_t)(ow[i] & 0xffffu);
         const uint32_t flags = (uint32_t)(x[i][6] >> 48);
         done_word[i] = 0;
         if (d >= p.nslots) {  // the host never writes such an entry; the advancer stops on it
@@ -364,18 +499,18 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
             ntiles = (uint32_t)((groups + tg - 1) / tg * tp);
         }
         SrvRec *rec = p.recs + d;
-        rec->rq.in = reinterpret_cast<const uint4 *>(in);
-        rec->rq.out = reinterpret_cast<uint4 *>(out);
-        rec->rq.len = len;
-        rec->rq.iv_hi = iv_hi;
-        rec->rq.iv_lo = iv_lo;
-        rec->rq.rk = p.keys + 15u * (ok && !emulated ? ks : 0u);
-        rec->rq.nr = (uint32_t)nr;
-        rec->rq.pad = flags;
-        rec->gen = x[i][5];
-        rec->done_tiles = 0;
-        rec->tile_groups = tg;
-        rec->tile_parts = tp;
+        st_field(&rec->rq.in, reinterpret_cast<const uint4 *>(in));
+        st_field(&rec->rq.out, reinterpret_cast<uint4 *>(out));
+        st_field(&rec->rq.len, len);
+        st_field(&rec->rq.iv_hi, iv_hi);
+        st_field(&rec->rq.iv_lo, iv_lo);
+        st_field(&rec->rq.rk, p.keys + 15u * (ok && !emulated ? ks : 0u));
+        st_field(&rec->rq.nr, (uint32_t)nr);
+        st_field(&rec->rq.pad, flags);
+        st_field(&rec->gen, (unsigned long long)x[i][5]);
+        st_field(&rec->done_tiles, 0u);
+        st_field(&rec->tile_groups, tg);
+        st_field(&rec->tile_parts, tp);
         ent[i] = ring_entry(k, d, ntiles);
         if (PER_REQ)  // with the record: a claim that sees the claim word below finds it
             st_relaxed_gpu(&rec->seq_ntiles, ((uint64_t)k << kTileBits) | ntiles);
@@ -655,8 +790,10 @@ SRV_FN uint32_t claim_pr(const SrvParams &p, uint32_t &cur, uint64_t &last_work,
                     }
                     return 0;
                 }
-                if (vs != cur && !seq_after(vs, cur))
+                if (vs != cur && !seq_after(vs, cur)) {
+                    SRV_STAT(stale_claim_retries);
                     continue;  // cur's claim word not seen yet (it precedes the ring entry): retry
+                }
                 if (vs != cur) {
                     // The slot was reaped and reused: this claim landed on the
                     // newer request vs, whose record is complete (its claim
@@ -671,6 +808,7 @@ SRV_FN uint32_t claim_pr(const SrvParams &p, uint32_t &cur, uint64_t &last_work,
                         *t1 = t + want < nt2 ? (uint32_t)t + want : nt2;
                         *nt_out = nt2;
                         last_work = gtime();
+                        SRV_STAT(recycled_claims);
                         return 0;
                     }
                 }
@@ -694,8 +832,10 @@ SRV_FN uint32_t claim_pr(const SrvParams &p, uint32_t &cur, uint64_t &last_work,
             last_work = gtime();
             continue;
         }
-        if (exhausted(p, low))  // repair: low stopped on a request that is exhausted
+        if (exhausted(p, low)) {  // repair: low stopped on a request that is exhausted
+            SRV_STAT(low_repairs);
             help_low(p, low);
+        }
         if (since(last_work) > (int64_t)p.idle_ns)
             return kExitIdle;
         nap(backoff);

@@ -9,9 +9,12 @@
 // which the GPU raises itself.
 //
 // Host -> device (pinned mapped memory):
-//   queue[i]   entry of request sequence number s at i = s mod Q (64 bytes):
-//              payload pointers, length, IV, key slot, descriptor slot d,
-//              generation, flags, and the tag s + 1 stored last (release)
+//   queue[d]   body of the request in descriptor slot d (64 bytes): payload
+//              pointers, length, IV, key slot, generation, flags
+//   order[i]   ((s + 1) << 16) | d for request sequence number s at
+//              i = s mod Q, stored (release) after the body: one load gives
+//              the device a request's slot, and the body stays put until the
+//              request completes
 //   stop       set by offload_server_destroy
 // Device -> host:
 //   done[d]    (generation << 2) | status, stored with st.release.sys once the last tile
@@ -277,7 +280,8 @@ struct offload_server_s {
     uint32_t qsize = 0;
     uint64_t budget = 0, max_len = 0, idle_ns = 0;
     // mapped host memory
-    QEntry *queue = nullptr;
+    QEntry *queue = nullptr;       // one body per descriptor slot
+    uint64_t *order = nullptr;     // qsize order words
     unsigned long long *done = nullptr;
     unsigned int *ctrl = nullptr;  // [0] stop, [1] kernel exit status
     // device memory
@@ -387,11 +391,13 @@ int enqueue(offload_server_s *s, uint32_t key_slot, uint64_t iv_hi, uint64_t iv_
     s->lens[d] = flags & kFlagEmulated ? 0 : len;
     const uint64_t tk = (gen << 16) | d;
     s->live[d].store(tk);
-    // A slot is admitted only while fewer than `slots` requests are in
-    // flight and the device reads entries in sequence order, so the entry of
-    // seq - qsize (qsize >= slots) has been read before this one reuses it.
+    // The body goes to the request's own slot, which it holds until it
+    // completes.  Its order word reuses the one of seq - qsize: a slot is
+    // admitted only while fewer than `slots` requests are in flight and the
+    // device reads order words in sequence order, so that word (qsize >=
+    // slots) has been read already.
     const uint64_t seq = s->next_seq.fetch_add(1);
-    QEntry &qe = s->queue[seq & (s->qsize - 1)];
+    QEntry &qe = s->queue[d];
     qe.in = (uint64_t)(uintptr_t)din;
     qe.out = (uint64_t)(uintptr_t)dout;
     qe.len = len;
@@ -401,7 +407,8 @@ int enqueue(offload_server_s *s, uint32_t key_slot, uint64_t iv_hi, uint64_t iv_
     qe.key_slot = key_slot;
     qe.desc = (uint16_t)d;
     qe.flags = (uint16_t)flags;
-    __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
+    qe.tag = seq + 1;
+    __atomic_store_n(&s->order[seq & (s->qsize - 1)], ((seq + 1) << 16) | d, __ATOMIC_RELEASE);
     s->n_sub.fetch_add(1);
     *ticket = tk;
     const int rc = ensure_running(s);
@@ -474,19 +481,23 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
             cudaStreamDestroy(s->setup);
         cudaFree(s->dmem);
         cudaFreeHost(s->queue);
+        cudaFreeHost(s->order);
         cudaFreeHost(s->done);
         cudaFreeHost(s->ctrl);
         delete s;
         return e == cudaErrorMemoryAllocation ? AES_ENOMEM : cuda_fail(e, where);
     };
     const unsigned flags = cudaHostAllocMapped | cudaHostAllocPortable;
-    if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->queue), sizeof(QEntry) * q, flags)))
+    if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->queue), sizeof(QEntry) * (size_t)slots, flags)))
         return fail("cudaHostAlloc(queue)");
+    if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->order), sizeof(uint64_t) * q, flags)))
+        return fail("cudaHostAlloc(order)");
     if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->done), sizeof(unsigned long long) * slots, flags)))
         return fail("cudaHostAlloc(done)");
     if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->ctrl), 64, flags)))
         return fail("cudaHostAlloc(ctrl)");
-    std::memset(s->queue, 0, sizeof(QEntry) * q);
+    std::memset(s->queue, 0, sizeof(QEntry) * (size_t)slots);
+    std::memset(s->order, 0, sizeof(uint64_t) * q);
     std::memset(s->done, 0, sizeof(unsigned long long) * slots);
     std::memset(s->ctrl, 0, 64);
     // device: cursor, adv and disp each on a 4 KiB page of their own (every
@@ -527,6 +538,9 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     if ((e = cudaHostGetDevicePointer(&dp, s->queue, 0)))
         return fail("cudaHostGetDevicePointer");
     P.queue = static_cast<const QEntry *>(dp);
+    if ((e = cudaHostGetDevicePointer(&dp, s->order, 0)))
+        return fail("cudaHostGetDevicePointer");
+    P.order = static_cast<const uint64_t *>(dp);
     if ((e = cudaHostGetDevicePointer(&dp, s->done, 0)))
         return fail("cudaHostGetDevicePointer");
     P.done = static_cast<unsigned long long *>(dp);
@@ -733,6 +747,7 @@ int offload_server_destroy(offload_server_t s)
     cudaStreamDestroy(s->setup);
     cudaFree(s->dmem);
     cudaFreeHost(s->queue);
+    cudaFreeHost(s->order);
     cudaFreeHost(s->done);
     cudaFreeHost(s->ctrl);
     delete s;

@@ -12,8 +12,9 @@
 // issues (the CTAs must stop with ERROR).  Logic only: host memory ordering
 // is not the GPU's.
 //
-// usage: served_protocol_sim mode ctas slots requests tile_blocks idle_us seed [scenario [chaos]]
-// (chaos n > 0: every protocol memory operation yields with probability 1/n)
+// usage: served_protocol_sim mode ctas slots requests tile_blocks idle_us seed [scenario [chaos [weak]]]
+// (chaos n > 0: every protocol memory operation yields with probability 1/n;
+//  weak 1: stores become visible late and out of order, as on the device)
 #include "served_protocol.cuh"
 
 #include <atomic>
@@ -70,7 +71,8 @@ struct Sim {
     SrvRec *recs = nullptr;
     std::vector<uint4> keys;
     std::vector<int> key_nr;
-    QEntry *queue = nullptr;
+    QEntry *queue = nullptr;  // one body per slot
+    std::vector<uint64_t> order;
     uint32_t qsize = 1;
     std::vector<unsigned long long> done;
     unsigned int ctrl[16] = {};
@@ -107,8 +109,9 @@ struct Sim {
         key_nr[2] = 12;  // key slot 3 stays unregistered: requests naming it are rejected
         while (qsize < (uint32_t)slots)
             qsize <<= 1;
-        queue = static_cast<QEntry *>(std::aligned_alloc(64, sizeof(QEntry) * qsize));
-        std::memset(queue, 0, sizeof(QEntry) * qsize);
+        queue = static_cast<QEntry *>(std::aligned_alloc(64, sizeof(QEntry) * (size_t)slots));
+        std::memset(queue, 0, sizeof(QEntry) * (size_t)slots);
+        order.assign(qsize, 0);
         done.assign((size_t)slots, 0);
         disp.v = 1;                 // sequence numbers start at 1
         cursor.v = mode ? 1 : 0;    // per-request claims: low starts at the first sequence number
@@ -120,6 +123,7 @@ struct Sim {
         P.keys = keys.data();
         P.key_nr = key_nr.data();
         P.queue = queue;
+        P.order = order.data();
         P.done = done.data();
         P.stop = &ctrl[0];
         P.kstatus = &ctrl[1];
@@ -187,6 +191,7 @@ struct Sim {
             if (code)
                 break;
         }
+        drain_stores();  // a CTA's stores are visible once it has exited
         c->exit_code.store(code);
         if ((code & kExitError) && scenario != 2)
             fail("agent stopped with ERROR");
@@ -220,6 +225,7 @@ struct Sim {
             process(tl);
             tile_finished(P, tl.d);
         }
+        drain_stores();
         live.fetch_sub(1);
     }
 
@@ -354,7 +360,7 @@ struct Sim {
             const uint64_t gn = ++gen[(size_t)d];
             owner[(size_t)d] = i;
             ++inflight;
-            QEntry &qe = queue[seq & (qsize - 1)];
+            QEntry &qe = queue[d];  // offload_submit's layout: body in the slot, then the order word
             qe.in = r.len && !r.emulated ? 0x100000 : 0;
             qe.out = r.len && !r.emulated ? 0x200000 : 0;
             qe.len = r.len;
@@ -364,7 +370,8 @@ struct Sim {
             qe.key_slot = (uint32_t)r.key_slot;
             qe.desc = (uint16_t)d;
             qe.flags = r.emulated ? (uint16_t)kFlagEmulated : 0;
-            __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
+            qe.tag = seq + 1;
+            __atomic_store_n(&order[seq & (qsize - 1)], ((seq + 1) << 16) | d, __ATOMIC_RELEASE);
             ++seq;
             ensure_running();
             reap();
@@ -391,9 +398,13 @@ struct Sim {
         }
         if (!errors.load() && tiles_done.load() != want_tiles)
             fail("%llu tiles processed, %llu expected", tiles_done.load(), want_tiles);
-        std::printf("%s mode=%d ctas=%d slots=%d requests=%d completed=%d tiles=%llu launches=%d %s\n",
+        const HostStats &hs = host_stats();
+        std::printf("%s mode=%d ctas=%d slots=%d requests=%d completed=%d tiles=%llu launches=%d "
+                    "stale_retries=%llu recycled=%llu repairs=%llu %s\n",
                     errors.load() ? "FAIL" : "OK", mode, nctas, slots, nreq, completed,
-                    (unsigned long long)tiles_done.load(), launches, first_error);
+                    (unsigned long long)tiles_done.load(), launches,
+                    (unsigned long long)hs.stale_claim_retries.load(), (unsigned long long)hs.recycled_claims.load(),
+                    (unsigned long long)hs.low_repairs.load(), first_error);
         std::free(recs);
         std::free(queue);
         return errors.load() ? 1 : 0;
@@ -427,10 +438,7 @@ struct Sim {
                 fail("no CTA reported STOP (status %llu)", __atomic_load_n(&ctrl[1], __ATOMIC_RELAXED));
         } else {
             what = "bad entry";
-            QEntry &qe = queue[seq & (qsize - 1)];
-            std::memset(&qe, 0, sizeof(qe));
-            qe.desc = 0xffff;
-            __atomic_store_n(&qe.tag, seq + 1, __ATOMIC_RELEASE);
+            __atomic_store_n(&order[seq & (qsize - 1)], ((seq + 1) << 16) | 0xffffu, __ATOMIC_RELEASE);
             if (!all_exit(10.0 + 2e-9 * (double)idle_ns))
                 fail("CTAs still running after an invalid queue entry");
             else if (!(__atomic_load_n(&ctrl[1], __ATOMIC_RELAXED) & kExitError))
@@ -449,8 +457,8 @@ struct Sim {
 
 int main(int argc, char **argv)
 {
-    if (argc < 8 || argc > 10) {
-        std::fprintf(stderr, "usage: %s mode ctas slots requests tile_blocks idle_us seed [scenario [chaos]]\n",
+    if (argc < 8 || argc > 11) {
+        std::fprintf(stderr, "usage: %s mode ctas slots requests tile_blocks idle_us seed [scenario [chaos [weak]]]\n",
                      argv[0]);
         return 2;
     }
@@ -464,5 +472,6 @@ int main(int argc, char **argv)
     s.seed = (uint32_t)std::atoi(argv[7]);
     s.scenario = argc >= 9 ? std::atoi(argv[8]) : 0;
     srvp::chaos_period() = argc >= 10 ? std::atoi(argv[9]) : 0;
+    srvp::weak_stores() = argc >= 11 && std::atoi(argv[10]) != 0;
     return s.run();
 }

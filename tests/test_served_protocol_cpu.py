@@ -87,3 +87,24 @@ def test_under_schedule_perturbation(sim, mode, case):
     producer interleave far more finely."""
     r = subprocess.run([sim, str(mode)] + [str(x) for x in case], capture_output=True, text=True, timeout=240)
     assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
+
+
+# ctas, slots, requests, tile_blocks, idle us, seed, scenario, chaos period, weak stores
+WEAK = [
+    (8, 8, 2000, 0, 2000, 81, 0, 0, 1),
+    (4, 2, 1000, 64, 2000, 82, 0, 3, 1),
+    (12, 32, 2000, 1024, 500, 83, 0, 0, 1),
+    (4, 16, 1000, 0, 5000, 84, 1, 0, 1),
+    (4, 16, 1000, 0, 5000, 85, 2, 0, 1),
+]
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["global_cursor", "per_request"])
+@pytest.mark.parametrize("case", WEAK, ids=[f"c{c[0]}s{c[1]}t{c[3]}sc{c[6]}ch{c[7]}" for c in WEAK])
+def test_with_weak_store_visibility(sim, mode, case):
+    """The same checks with stores that become visible late and out of order
+    unless a fence orders them, as the device's relaxed stores may: every
+    fence the protocol relies on is exercised (the per-request dispatch
+    without its fence fails here)."""
+    r = subprocess.run([sim, str(mode)] + [str(x) for x in case], capture_output=True, text=True, timeout=240)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
