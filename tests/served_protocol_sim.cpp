@@ -375,8 +375,21 @@ struct Sim {
             ++seq;
             ensure_running();
             reap();
-            if (scenario && i == nreq / 2)
+            if (scenario && i == nreq / 2) {
+                // The invalid entry takes the next order word without a slot,
+                // so first let every request complete (it must not reuse the
+                // order word of one that is not dispatched yet).
+                while (scenario == 2 && inflight > 0 && !errors.load()) {
+                    reap();
+                    ensure_running();
+                    if (timed_out()) {
+                        fail("%llu requests never completed", (uint64_t)inflight);
+                        break;
+                    }
+                    std::this_thread::yield();
+                }
                 return finish_scenario(seq, inflight);
+            }
         }
         while (inflight > 0 && !errors.load()) {
             reap();
@@ -439,10 +452,23 @@ struct Sim {
         } else {
             what = "bad entry";
             __atomic_store_n(&order[seq & (qsize - 1)], ((seq + 1) << 16) | 0xffffu, __ATOMIC_RELEASE);
-            if (!all_exit(10.0 + 2e-9 * (double)idle_ns))
-                fail("CTAs still running after an invalid queue entry");
-            else if (!(__atomic_load_n(&ctrl[1], __ATOMIC_RELAXED) & kExitError))
-                fail("no CTA reported ERROR (status %llu)", __atomic_load_n(&ctrl[1], __ATOMIC_RELAXED));
+            // Like offload_poll's relaunch rule: a launch that ended idle (its
+            // CTAs left just as requests arrived) is relaunched; one that ended
+            // with ERROR is not.
+            const auto t0 = std::chrono::steady_clock::now();
+            for (;;) {
+                if (!all_exit(10.0 + 2e-9 * (double)idle_ns)) {
+                    fail("CTAs still running after an invalid queue entry");
+                    break;
+                }
+                if (__atomic_load_n(&ctrl[1], __ATOMIC_RELAXED) & kExitError)
+                    break;
+                if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(30)) {
+                    fail("no CTA reported ERROR (status %llu)", __atomic_load_n(&ctrl[1], __ATOMIC_RELAXED));
+                    break;
+                }
+                launch();
+            }
             __atomic_store_n(&ctrl[0], 1u, __ATOMIC_RELAXED);
         }
         std::printf("%s mode=%d scenario=%s ctas=%d tiles=%llu status=%u %s\n", errors.load() ? "FAIL" : "OK",
