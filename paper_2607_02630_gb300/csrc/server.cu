@@ -362,7 +362,7 @@ void release_slot(offload_server_s *s, uint32_t d)
 // Admission (HBM budget, then a free slot), the body of one request in its
 // slot and, stored last with release semantics, its order word.  Submitters
 // may race: if the order word of seq s is not stored yet, the device waits
-// at s, so every later request stays in flight holding a slot and seq +
+// at s, so every later request stays in flight holding a slot and s +
 // qsize cannot be admitted before that word has been read.
 int enqueue(offload_server_s *s, uint32_t key_slot, uint64_t iv_hi, uint64_t iv_lo, const void *din, void *dout,
             uint64_t len, uint32_t flags, uint64_t charge, uint64_t *ticket)
