@@ -349,19 +349,40 @@ inline unsigned long long atom_exch(unsigned long long *p, unsigned long long v)
 }
 #endif
 
-// A plain store to a record field (on the host, a weak store).
+// Plain and volatile accesses to records and to the CTA's shared ring, and
+// the CTA-scope fence (on the host, weak stores and a drain).
 #ifdef __CUDACC__
 template <class T>
 SRV_INLINE void st_field(T *p, T v)
 {
     *p = v;
 }
+template <class T>
+SRV_INLINE T ld_field(const T *p)
+{
+    return *p;
+}
+SRV_INLINE uint32_t ld_vol(const volatile unsigned int *p) { return *p; }
+SRV_INLINE void st_vol(volatile unsigned int *p, uint32_t v) { *p = v; }
+SRV_INLINE void fence_cta() { __threadfence_block(); }
 #define SRV_STAT(field) ((void)0)
 #else
 template <class T>
 inline void st_field(T *p, T v)
 {
     st_weak(p, v);
+}
+template <class T>
+inline T ld_field(const T *p)
+{
+    return ld_weak(p);
+}
+inline uint32_t ld_vol(const volatile unsigned int *p) { return ld_weak(const_cast<const unsigned int *>(p)); }
+inline void st_vol(volatile unsigned int *p, uint32_t v) { st_weak(const_cast<unsigned int *>(p), (unsigned int)v); }
+inline void fence_cta()
+{
+    drain_stores();
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
 }
 // How often host runs take the protocol's rare paths.
 struct HostStats {
@@ -897,6 +918,99 @@ SRV_INLINE void tile_finished(const SrvParams &p, uint32_t d)
         fence_sys();
         st_release_sys(p.done + d, (ld_cg(&rec->gen) << 2) | 1u);
     }
+}
+
+
+// ---- the CTA: agent and worker warps, joined by a ring in shared memory ----
+// The agent (warp 0, lane 0) claims tiles and pushes them; each worker warp's
+// lane 0 reserves the next position (atomicAdd on head) and waits for the
+// agent to fill it.  A slot is refilled only once the worker that read its
+// previous item has marked it read.
+struct Ring {
+    unsigned int head;               // positions reserved by workers (atomicAdd)
+    volatile unsigned int tail;      // positions filled by the agent
+    volatile unsigned int exit_code; // set by the agent after its last push
+    uint32_t d[kRing], t[kRing], seq[kRing];
+    volatile unsigned int read_mark[kRing];  // position + 1 of the last item read from each slot
+};
+
+// Agent warp, lane 0: keep the ring kPrefetch items ahead of the workers.
+// PER_REQ selects per-request claims (claim_mode 1) over the global cursor.
+template <bool PER_REQ>
+SRV_NOINLINE void agent(const SrvParams &p, Ring &ring)
+{
+    uint64_t last_work = gtime();
+    StopCheck stop;
+    uint32_t cur = PER_REQ ? (uint32_t)ld_relaxed_gpu(p.cursor) : 0u;  // request this agent stands on
+    uint32_t ld = 0, lseq = 0, lt = 0, lend = 0;  // current lease: tiles [lt, lend) of slot ld
+    bool adv_after = false;                      // the lease ends its request
+    uint32_t code = 0;
+    uint32_t backoff = 32;  // ns; a spinning agent would take shared-memory cycles from its workers
+    for (;;) {
+        const uint32_t head = ld_vol(reinterpret_cast<volatile unsigned int *>(&ring.head));
+        const uint32_t tail = ld_vol(&ring.tail);
+        // full: kPrefetch items already wait for workers, or the item that
+        // position tail would overwrite (tail - kRing) has not been read yet
+        if ((int32_t)(tail - head) >= (int32_t)kPrefetch ||
+            (tail >= kRing && ld_vol(&ring.read_mark[tail % kRing]) != tail - kRing + 1)) {
+            if (stop(p.stop)) {
+                code = kExitStop;
+                break;
+            }
+            nap(backoff);
+            backoff = backoff < 256 ? 2 * backoff : 256;
+            continue;
+        }
+        if (lt >= lend) {
+            const uint32_t waiting = (int32_t)(head - tail) > 0 ? head - tail : 0u;
+            const uint32_t want = waiting + kPrefetch < kMaxClaim ? waiting + kPrefetch : kMaxClaim;
+            code = agent_claim<PER_REQ>(p, cur, last_work, stop, want, &ld, &lseq, &lt, &lend, adv_after);
+            if (code)
+                break;
+        }
+        const uint32_t slot = tail % kRing;
+        st_field(&ring.d[slot], ld);
+        st_field(&ring.t[slot], lt);
+        st_field(&ring.seq[slot], lseq);
+        ++lt;
+        backoff = 32;
+        fence_cta();
+        st_vol(&ring.tail, tail + 1);
+        if (lt >= lend) {  // the whole lease is queued
+            code = lease_queued<PER_REQ>(p, cur, lseq, adv_after, last_work, stop);
+            if (code)
+                break;
+        }
+    }
+    fence_cta();
+    st_vol(&ring.exit_code, code);
+}
+
+// A worker warp's lane 0: take the next position and wait for the agent to
+// fill it.  Returns false when the agent has exited without filling it (its
+// last pushes are taken first).
+SRV_INLINE bool ring_pop(Ring &ring, uint32_t *d, uint32_t *t, uint32_t *seq)
+{
+    const uint32_t pos = atom_add(&ring.head, 1u);
+    for (uint32_t spin = 0;; ++spin) {
+        if ((int32_t)(ld_vol(&ring.tail) - pos) > 0)
+            break;
+        if (spin > 4)
+            nap(64);
+        if (ld_vol(&ring.exit_code)) {
+            fence_cta();
+            if ((int32_t)(ld_vol(&ring.tail) - pos) <= 0)
+                return false;
+            break;
+        }
+    }
+    fence_cta();
+    *d = ld_field(&ring.d[pos % kRing]);
+    *t = ld_field(&ring.t[pos % kRing]);
+    *seq = ld_field(&ring.seq[pos % kRing]);
+    fence_cta();
+    st_vol(&ring.read_mark[pos % kRing], pos + 1);
+    return true;
 }
 
 }  // namespace srvp

@@ -105,66 +105,6 @@ __device__ __forceinline__ void run_part_regs(const aesrt::BatchReq &rq, uint64_
                                ln, rk);
 }
 
-struct Ring {
-    unsigned int head;               // positions reserved by workers (atomicAdd)
-    volatile unsigned int tail;      // positions filled by the agent
-    volatile unsigned int exit_code; // set by the agent after its last push
-    uint32_t d[kRing], t[kRing], seq[kRing];
-    volatile unsigned int read_mark[kRing];  // position + 1 of the last item read from each slot
-};
-
-// Agent warp, lane 0: keep the ring kPrefetch items ahead of the workers.
-// PER_REQ selects per-request claims (claim_mode 1) over the global cursor.
-template <bool PER_REQ>
-__device__ __noinline__ void agent(const SrvParams &p, Ring &ring)
-{
-    uint64_t last_work = gtime();
-    StopCheck stop;
-    uint32_t cur = PER_REQ ? (uint32_t)ld_relaxed_gpu(p.cursor) : 0u;  // request this agent stands on
-    uint32_t ld = 0, lseq = 0, lt = 0, lend = 0;  // current lease: tiles [lt, lend) of slot ld
-    bool adv_after = false;                      // the lease ends its request
-    uint32_t code = 0;
-    uint32_t backoff = 32;  // ns; a spinning agent would take shared-memory cycles from its workers
-    for (;;) {
-        const uint32_t head = *reinterpret_cast<volatile unsigned int *>(&ring.head);
-        const uint32_t tail = ring.tail;
-        // full: kPrefetch items already wait for workers, or the item that
-        // position tail would overwrite (tail - kRing) has not been read yet
-        if ((int32_t)(tail - head) >= (int32_t)kPrefetch ||
-            (tail >= kRing && ring.read_mark[tail % kRing] != tail - kRing + 1)) {
-            if (stop(p.stop)) {
-                code = kExitStop;
-                break;
-            }
-            __nanosleep(backoff);
-            backoff = backoff < 256 ? 2 * backoff : 256;
-            continue;
-        }
-        if (lt >= lend) {
-            const uint32_t waiting = (int32_t)(head - tail) > 0 ? head - tail : 0u;
-            const uint32_t want = waiting + kPrefetch < kMaxClaim ? waiting + kPrefetch : kMaxClaim;
-            code = agent_claim<PER_REQ>(p, cur, last_work, stop, want, &ld, &lseq, &lt, &lend, adv_after);
-            if (code)
-                break;
-        }
-        const uint32_t slot = tail % kRing;
-        ring.d[slot] = ld;
-        ring.t[slot] = lt;
-        ring.seq[slot] = lseq;
-        ++lt;
-        backoff = 32;
-        __threadfence_block();
-        ring.tail = tail + 1;
-        if (lt >= lend) {  // the whole lease is queued
-            code = lease_queued<PER_REQ>(p, cur, lseq, adv_after, last_work, stop);
-            if (code)
-                break;
-        }
-    }
-    __threadfence_block();
-    ring.exit_code = code;
-}
-
 template <bool PER_REQ>
 __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ SrvParams p)
 {
@@ -193,28 +133,8 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
     aesrt::BatchReq rq;
     for (;;) {
         uint32_t d = 0, t = 0, seq = 0, quit = 0;
-        if (lane == 0) {
-            const uint32_t pos = atomicAdd(&ring.head, 1u);
-            for (uint32_t spin = 0;; ++spin) {
-                if ((int32_t)(ring.tail - pos) > 0)
-                    break;
-                if (spin > 4)
-                    __nanosleep(64);
-                if (ring.exit_code) {
-                    __threadfence_block();
-                    quit = (int32_t)(ring.tail - pos) <= 0;  // the agent's last pushes come first
-                    break;
-                }
-            }
-            if (!quit) {
-                __threadfence_block();
-                d = ring.d[pos % kRing];
-                t = ring.t[pos % kRing];
-                seq = ring.seq[pos % kRing];
-                __threadfence_block();
-                ring.read_mark[pos % kRing] = pos + 1;
-            }
-        }
+        if (lane == 0)
+            quit = !ring_pop(ring, &d, &t, &seq);
         quit = __shfl_sync(0xffffffffu, quit, 0);
         if (quit)
             break;

@@ -1,9 +1,9 @@
 // served_protocol_sim.cpp -- host threads stand in for the served kernel's
 // resident CTAs and run its request protocol (served_protocol.cuh, compiled
 // for the host) against a producer that submits and reaps requests the way
-// offload_submit / offload_poll do.  Each CTA is an agent thread (claims
-// tiles, queues them) and a worker thread (takes queued tiles, finishes
-// them).  Checked: every tile of every request is processed exactly once
+// offload_submit / offload_poll do.  Each CTA is an agent thread running
+// the kernel's agent loop and two worker threads taking tiles from the
+// kernel's shared ring, as the kernel's worker warps do.  Checked: every tile of every request is processed exactly once
 // and while its request still owns the slot, every request completes once
 // with the right status, zero-length and rejected requests complete at
 // dispatch, emulated offloads take one tile, and idle exits and relaunches
@@ -32,7 +32,6 @@ using namespace srvp;
 namespace {
 
 constexpr int kMaxKeys = 4;
-constexpr uint32_t kQueueCap = 16;  // tiles an agent keeps queued
 
 struct alignas(64) Word {
     unsigned long long v = 0;
@@ -53,12 +52,11 @@ struct Tile {
     uint32_t d, t, seq;
 };
 
-// One stand-in CTA: agent + worker sharing a small queue.
+// One stand-in CTA: the agent and kWorkers worker warps, joined by the
+// kernel's own shared ring (served_protocol.cuh).
+constexpr int kWorkers = 2;
 struct Cta {
-    std::mutex mu;
-    std::vector<Tile> q;
-    std::atomic<bool> agent_done{false};
-    std::atomic<uint32_t> exit_code{0};
+    Ring ring{};
 };
 
 struct Sim {
@@ -154,74 +152,29 @@ struct Sim {
         return (uint32_t)((groups + tg - 1) / tg * tp);
     }
 
+    // The agent warp's lane 0: the kernel's own agent loop, then what the
+    // kernel does with its exit code.
     template <bool PER_REQ>
-    void agent(Cta *c)
+    void agent_thread(Cta *c)
     {
-        uint64_t last_work = gtime();
-        StopCheck stop;
-        uint32_t cur = PER_REQ ? (uint32_t)ld_relaxed_gpu(P.cursor) : 0u;
-        bool adv_after = false;
-        uint32_t code = 0;
-        for (;;) {
-            bool full;
-            {
-                std::lock_guard<std::mutex> lk(c->mu);
-                full = c->q.size() >= kQueueCap;
-            }
-            if (full) {  // let the worker catch up
-                if (stop(P.stop)) {
-                    code = kExitStop;
-                    break;
-                }
-                std::this_thread::yield();
-                continue;
-            }
-            uint32_t d = 0, seq = 0, t0 = 0, t1 = 0;
-            code = agent_claim<PER_REQ>(P, cur, last_work, stop, kMaxClaim, &d, &seq, &t0, &t1, adv_after);
-            if (code)
-                break;
-            if (t1 <= t0 || t1 - t0 > kMaxClaim)
-                fail("claim of %llu..%llu tiles of seq %llu", t0, t1, seq);
-            {
-                std::lock_guard<std::mutex> lk(c->mu);
-                for (uint32_t t = t0; t < t1; ++t)
-                    c->q.push_back(Tile{d, t, seq});
-            }
-            code = lease_queued<PER_REQ>(P, cur, seq, adv_after, last_work, stop);
-            if (code)
-                break;
-        }
-        drain_stores();  // a CTA's stores are visible once it has exited
-        c->exit_code.store(code);
+        srvp::agent<PER_REQ>(P, c->ring);
+        const uint32_t code = ld_vol(&c->ring.exit_code);
         if ((code & kExitError) && scenario != 2)
             fail("agent stopped with ERROR");
-        __atomic_fetch_or(P.kstatus, code, __ATOMIC_RELAXED);
-        c->agent_done.store(true);
+        if (code)
+            __atomic_fetch_or(P.kstatus, code, __ATOMIC_RELAXED);
+        drain_stores();  // a CTA's stores are visible once it has exited
+        live.fetch_sub(1);
     }
 
-    void worker(Cta *c)
+    // A worker warp's lane 0: the kernel's ring_pop, the tile (checked here
+    // instead of encrypted) and the kernel's completion step.
+    void worker_thread(Cta *c)
     {
         for (;;) {
             Tile tl{};
-            bool have = false;
-            {
-                std::lock_guard<std::mutex> lk(c->mu);
-                if (!c->q.empty()) {
-                    tl = c->q.front();
-                    c->q.erase(c->q.begin());
-                    have = true;
-                }
-            }
-            if (!have) {
-                if (c->agent_done.load()) {
-                    std::lock_guard<std::mutex> lk(c->mu);
-                    if (c->q.empty())
-                        break;
-                    continue;
-                }
-                std::this_thread::yield();
-                continue;
-            }
+            if (!ring_pop(c->ring, &tl.d, &tl.t, &tl.seq))
+                break;
             process(tl);
             tile_finished(P, tl.d);
         }
@@ -260,15 +213,16 @@ struct Sim {
         ctas.clear();
         ctrl[1] = 0;
         ++launches;
-        live.store(nctas);
+        live.store(nctas * (1 + kWorkers));
         for (int i = 0; i < nctas; ++i) {
             ctas.emplace_back(new Cta());
             Cta *c = ctas.back().get();
             if (mode)
-                threads.emplace_back([this, c] { agent<true>(c); });
+                threads.emplace_back([this, c] { agent_thread<true>(c); });
             else
-                threads.emplace_back([this, c] { agent<false>(c); });
-            threads.emplace_back([this, c] { worker(c); });
+                threads.emplace_back([this, c] { agent_thread<false>(c); });
+            for (int w = 0; w < kWorkers; ++w)
+                threads.emplace_back([this, c] { worker_thread(c); });
         }
     }
 
