@@ -51,9 +51,10 @@
 // record: agents walk the dispatched requests in order on their own, so
 // several requests are cut into tiles at once (cursor then holds `low`, the
 // oldest request that may have unclaimed tiles).  The protocol -- layouts,
-// dispatch, both claim modes, completion -- is in served_protocol.cuh; this
-// file holds the CTA structure (agent, shared-memory ring, workers) and the
-// host side.
+// dispatch, both claim modes, the agent loop, the agent-worker ring and
+// completion -- is in served_protocol.cuh, which also compiles for host
+// threads; this file holds the kernel (the workers' tile loop) and the host
+// side.
 #include "../../include/aesoffload.h"
 #include "internal.h"
 #include "runtime.h"
