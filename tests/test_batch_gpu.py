@@ -199,3 +199,14 @@ def test_in_place_batch_matches_oracle(cuda, aes, ncpu):
         got = out_src[o: o + n] if k % 2 == 0 else out_dst[o: o + n]
         np.testing.assert_array_equal(got, oracle.ctr_mt(key, b, iv, payload[o: o + n], ncpu),
                                       err_msg=f"request {k} len {n}")
+
+
+@pytest.mark.parametrize("bits", [128, 256])
+def test_batch_every_length_0_to_64(cuda, aes, ncpu, bits):
+    """One batch of 65 requests, of every length from 0 to 64 bytes (each
+    tail u = 1..15 of a partial final block several times over)."""
+    g = W.rng(53 + bits)
+    lengths = list(range(65))
+    reqs, meta, payload, src, dst = make_requests(cuda, aes, g, lengths, [bits] * len(lengths))
+    aes.batch(reqs, tile_blocks=1024)
+    check_all(cuda, meta, payload, dst, ncpu)

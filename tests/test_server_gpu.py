@@ -634,3 +634,29 @@ def test_served_in_place_matches_oracle(cuda, aes, ncpu):
             np.testing.assert_array_equal(out[o: o + n], oracle.ctr_mt(key, 256, ivs[i], payload[o: o + n], ncpu))
     finally:
         assert srv.close() == aes.AES_OK
+
+
+@pytest.mark.parametrize("bits", [128, 256])
+def test_served_every_length_0_to_64(cuda, aes, ncpu, bits):
+    """Served requests of every length from 0 to 64 bytes, all in flight
+    together; bytes past each length stay untouched."""
+    srv = aes.Server(slots=128, max_keys=1, ctas=16, idle_timeout_us=500_000)
+    try:
+        g = W.rng(71 + bits)
+        key = W.random_bytes(g, bits // 8)
+        slot = srv.key_register(key.tobytes(), bits)
+        sizes = list(range(65))
+        payload, offs, src, dst = arena(cuda, g, sizes)
+        ivs = [W.random_bytes(g, 16) for _ in sizes]
+        tickets = [srv.submit(slot, ivs[i].tobytes(), src.data_ptr() + int(offs[i]), dst.data_ptr() + int(offs[i]),
+                              n) for i, n in enumerate(sizes)]
+        for t in tickets:
+            assert srv.wait(t, WAIT_US) == aes.AES_OK
+        out = to_host(dst)
+        for i, n in enumerate(sizes):
+            o = int(offs[i])
+            np.testing.assert_array_equal(out[o: o + n], oracle.ctr(key, bits, ivs[i], payload[o: o + n]),
+                                          err_msg=f"len={n}")
+            assert (out[o + n: o + n + 16] == 0xA5).all(), f"bytes past len {n} were written"
+    finally:
+        assert srv.close() == aes.AES_OK
