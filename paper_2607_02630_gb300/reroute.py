@@ -94,6 +94,7 @@ class ServedOffload:
                 break
             if rc != self.aes.AES_EAGAIN:
                 raise self.aes.AesError(rc, "offload_submit")
+            time.sleep(0)  # back-pressure: let the completion thread free a slot
         with self.lock:
             self.pending[ticket] = (loop, fut)
         self.wake.set()
