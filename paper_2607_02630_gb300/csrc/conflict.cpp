@@ -76,6 +76,8 @@ struct Fiber {
     bool snap_valid = false;    // has parked during the current request
     uint64_t snapshot = 0;      // version clock when it last parked
     uint64_t ticket = 0;        // offload in flight (server)
+    bool finished = false;      // its completion was reaped on its behalf (finished_rc)
+    int finished_rc = 0;
     uint64_t reads = 0;         // CDET_PATTERN_READONLY: reads completed
     clk::time_point deadline;   // offload in flight (host timer)
     int dirty_lo = 0, dirty_hi = -1;  // pages this handler unprotected: within [lo, hi]
@@ -308,12 +310,34 @@ bool offload_done(Run &r, Fiber &f)
 {
     if (!r.cfg.srv)
         return clk::now() >= f.deadline;
-    const int rc = offload_poll(r.cfg.srv, f.ticket);
+    int rc;
+    if (f.finished) {
+        f.finished = false;
+        rc = f.finished_rc;
+    } else {
+        rc = offload_poll(r.cfg.srv, f.ticket);
+    }
     if (rc == AES_PENDING)
         return false;
     if (rc != AES_OK && !r.error)
         r.error = rc;
     return true;
+}
+
+// Reap, on their behalf, the completed offloads of other parked handlers:
+// their slots are freed without any other handler running, so a handler
+// waiting for a slot (or a serialized one) keeps its place in the order.
+void reap_others(Run &r, Fiber &self)
+{
+    for (auto &g : r.fibers) {
+        if (&g == &self || !g.parked || g.finished)
+            continue;
+        const int rc = offload_poll(r.cfg.srv, g.ticket);
+        if (rc != AES_PENDING) {
+            g.finished = true;
+            g.finished_rc = rc;
+        }
+    }
 }
 
 bool offload_start(Run &r, Fiber &f, int req)
@@ -322,6 +346,7 @@ bool offload_start(Run &r, Fiber &f, int req)
         f.deadline = clk::now() + std::chrono::nanoseconds(r.cfg.offload_ns);
         return true;
     }
+    const clk::time_point t0 = clk::now();
     for (;;) {
         int rc;
         if (r.cfg.bytes) {
@@ -336,11 +361,17 @@ bool offload_start(Run &r, Fiber &f, int req)
         }
         if (rc == AES_OK)
             return true;
+        if (rc == AES_EAGAIN && clk::now() - t0 > std::chrono::seconds(30))
+            rc = AES_ETIMEOUT;  // no slot freed: the server is stuck
         if (rc != AES_EAGAIN) {
             if (!r.error)
                 r.error = rc;
             return false;
         }
+        // Every slot is held (more handlers than server slots): the holders
+        // are parked handlers, whose completions only the event loop would
+        // reap, and it cannot run while this handler waits here.
+        reap_others(r, f);
     }
 }
 

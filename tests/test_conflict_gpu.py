@@ -63,3 +63,17 @@ def test_safe_patterns_with_served_emulated_offload(cuda, aes, pattern):
         assert r["conflicts"] == 0 and r["lost_updates"] == 0 and r["final_count"] == 1000, r
     finally:
         assert srv.close() == aes.AES_OK
+
+
+def test_more_handlers_than_server_slots(cuda, aes):
+    """16 handlers on a server with 4 request slots: a handler that finds
+    every slot held reaps the parked handlers' completions itself (the event
+    loop cannot run meanwhile), so the run completes; enforcement still loses
+    nothing."""
+    srv = aes.Server(slots=4, max_keys=1, ctas=16, idle_timeout_us=500_000)
+    try:
+        r = aes.conflict_run(aes.CDET_ENFORCE, handlers=16, requests=1000, counters=16, offload_ns=20_000,
+                             server=srv)
+        assert r["lost_updates"] == 0 and r["final_count"] == 1000, r
+    finally:
+        assert srv.close() == aes.AES_OK
