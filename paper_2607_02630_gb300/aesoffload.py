@@ -214,15 +214,20 @@ def _bytes16(iv) -> ctypes.Array:
     return (ctypes.c_uint8 * 16).from_buffer_copy(b)
 
 
-def _keybuf(key) -> bytes:
-    return bytes(bytearray(key if isinstance(key, (bytes, bytearray)) else memoryview(key).tobytes()))
+def _keybuf(key, bits: int) -> bytes:
+    """The key's bytes; the library reads bits / 8 of them, so a shorter key
+    is refused here (a key size the library rejects is passed through)."""
+    kb = bytes(bytearray(key if isinstance(key, (bytes, bytearray)) else memoryview(key).tobytes()))
+    if int(bits) in (128, 192, 256) and len(kb) < int(bits) // 8:
+        raise ValueError(f"a {bits}-bit key needs {int(bits) // 8} bytes, got {len(kb)}")
+    return kb
 
 
 class Context:
     """A device-resident AES key schedule (aes_ctx_create)."""
 
     def __init__(self, key, bits: int):
-        kb = _keybuf(key)
+        kb = _keybuf(key, bits)
         h = ctypes.c_void_p()
         buf = ctypes.create_string_buffer(kb, max(len(kb), 1))
         _check(lib().aes_ctx_create(ctypes.byref(h), buf, int(bits)), "aes_ctx_create")
@@ -348,7 +353,7 @@ class Server:
 
     def key_register(self, key, bits: int) -> int:
         slot = ctypes.c_int(-1)
-        kb = _keybuf(key)
+        kb = _keybuf(key, bits)
         buf = ctypes.create_string_buffer(kb, max(len(kb), 1))
         _check(lib().offload_key_register(self.handle, buf, int(bits), ctypes.byref(slot)),
                "offload_key_register")

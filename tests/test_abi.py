@@ -152,3 +152,14 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     assert got[("aes_drive_req_t", "size")] == drive.itemsize
     for f in drive.names:
         assert got[("aes_drive_req_t", f)] == drive.fields[f][1], f
+
+
+def test_short_keys_are_refused_before_the_library_reads_them():
+    """The library reads bits / 8 key bytes; the binding refuses a shorter key
+    instead of letting it read past the caller's buffer."""
+    with pytest.raises(ValueError):
+        A._keybuf(bytes(16), 256)
+    with pytest.raises(ValueError):
+        A._keybuf(bytes(23), 192)
+    assert A._keybuf(bytes(32), 256) == bytes(32)
+    assert A._keybuf(b"x", 64) == b"x"  # a key size the library rejects itself (AES_EKEYBITS)
