@@ -261,8 +261,9 @@ typedef struct {
  * stream of its own.  Errors: AES_EINVAL, AES_ENOMEM, AES_ECUDA. */
 int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg);
 
-/* Expand `key` into resident key slot *slot_out (device kernel, FIPS-197
- * Sec. 5.2).  Thread-safe.  AES_ETOOBIG when all max_keys slots are used.
+/* Expand `key` (host pointer, bits/8 bytes; bits in {128, 192, 256}) into
+ * resident key slot *slot_out (device kernel, FIPS-197 Sec. 5.2).
+ * Thread-safe.  AES_ETOOBIG when all max_keys slots are used.
  * May be called while the resident kernel runs: the expansion kernel runs on
  * the SMs the resident kernel leaves free (ctas < SM count, the default), and
  * the resident kernel reads round keys through L2, so a request submitted
