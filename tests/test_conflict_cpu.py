@@ -146,3 +146,23 @@ def test_protection_changes_per_guarded_write():
     assert plain["final_count"] == n and emu["final_count"] == n
     assert plain["protect_calls"] == 2 * n and plain["emulated_stores"] == 0
     assert emu["protect_calls"] == 0 and emu["emulated_stores"] == n
+
+
+@pytest.mark.parametrize("opt", ["-O0", "-O2"])
+def test_detector_under_undefined_behaviour_sanitizer(tmp_path, opt):
+    """conflict.cpp built on its own with -fsanitize=undefined (any finding
+    aborts), run over every mode and pattern with and without store
+    emulation, and its store self-test (the compiler's store forms differ
+    between -O0 and -O2)."""
+    import os
+    import subprocess
+
+    from paper_2607_02630_gb300 import build as B
+
+    exe = str(tmp_path / "cdet_ubsan")
+    here = os.path.dirname(os.path.abspath(__file__))
+    subprocess.run(["g++", opt, "-g", "-std=c++17", "-fsanitize=undefined", "-fno-sanitize-recover=undefined",
+                    "-I", B.INCLUDE, os.path.join(here, "conflict_ubsan_main.cpp"),
+                    os.path.join(B.CSRC, "conflict.cpp"), "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "OK selftest rc=0" in r.stdout, r.stdout + r.stderr
