@@ -25,7 +25,9 @@ def sim(tmp_path_factory):
     nvcc = B._nvcc()
     cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
     exe = str(tmp_path_factory.mktemp("sim") / "served_protocol_sim")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", "-Wall", "-Wno-unknown-pragmas", "-I", B.INCLUDE,
+    # undefined behaviour aborts the run (and so fails the test)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", "-Wall", "-Wno-unknown-pragmas", "-fsanitize=undefined",
+                    "-fno-sanitize-recover=undefined", "-I", B.INCLUDE,
                     "-I", B.CSRC, "-I", cuda_inc, os.path.join(HERE, "served_protocol_sim.cpp"), "-o", exe],
                    check=True)
     return exe
