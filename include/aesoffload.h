@@ -244,6 +244,11 @@ typedef struct {
                                1 = per-request claim words that agents walk in
                                sequence order, several requests cut at once
                                (experimental: not yet measured) */
+    int trace_requests;     /* trace builds (libaesoffload_trace.so): keep timer
+                               stamps of the protocol's steps for the last
+                               trace_requests requests (a power of two up to
+                               2^20; 0 = off); read with offload_server_trace.
+                               Other builds refuse a nonzero value (AES_EINVAL). */
 } offload_cfg_t;
 
 typedef struct {
@@ -312,6 +317,18 @@ int offload_poll_many(offload_server_t srv, const uint64_t *tickets, int n, int 
 int offload_wait(offload_server_t srv, uint64_t ticket, uint64_t timeout_us);
 
 int offload_server_stats(offload_server_t srv, offload_stats_t *out);
+
+/* Trace builds: copy the stamp buffer (trace_requests rows of
+ * AES_TRACE_POINTS %globaltimer values in ns; row s & (trace_requests - 1)
+ * belongs to request sequence number s, counted from 1 in submit order; 0 =
+ * not reached) into `out`, at most `max_words` values.  The points, in order:
+ * dispatched (its order word claimed), published (record complete, ring
+ * entry about to be stored), first tile claimed, first tile taken by a
+ * worker, record loaded, round keys loaded, first tile done, completion
+ * raised.  Returns the number
+ * of values copied; AES_EINVAL without tracing. */
+#define AES_TRACE_POINTS 8
+int offload_server_trace(offload_server_t srv, uint64_t *out, size_t max_words);
 
 /* Raise the stop flag, wait (bounded, 5 s) for the resident kernel to exit,
  * and free everything.  Requests still in flight are abandoned.  Returns

@@ -36,6 +36,7 @@ VARIANT_BITSLICE = 2
 
 _lock = threading.Lock()
 _lib = None
+_lib_path = None  # set by use_trace_build() before the first call
 
 
 class AesError(RuntimeError):
@@ -64,7 +65,8 @@ class BatchOpts(ctypes.Structure):
 class ServerCfg(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_keys", ctypes.c_int), ("hbm_budget", ctypes.c_uint64),
                 ("ctas", ctypes.c_int), ("threads", ctypes.c_int), ("tile_blocks", ctypes.c_int),
-                ("idle_timeout_us", ctypes.c_uint32), ("claim_mode", ctypes.c_int)]
+                ("idle_timeout_us", ctypes.c_uint32), ("claim_mode", ctypes.c_int),
+                ("trace_requests", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -141,6 +143,7 @@ _SIGS = {
     "offload_drive_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(DriveOpts), ctypes.c_void_p, ctypes.POINTER(DriveResult)]),
     "cdet_run": (ctypes.c_int, [ctypes.POINTER(CdetCfg), ctypes.POINTER(CdetResult)]),
+    "offload_server_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t]),
     "cdet_store_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                            ctypes.POINTER(ctypes.c_uint64)]),
     "offload_drive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -151,7 +154,20 @@ _SIGS = {
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _lib_path or _build.LIB
+
+
+def use_trace_build() -> str:
+    """Load libaesoffload_trace.so (the served kernel with per-request timer
+    stamps compiled in; see Server.trace) instead of libaesoffload.so.  Call
+    before anything else uses the library in this process; builds it if
+    needed."""
+    global _lib_path
+    with _lock:
+        if _lib is not None and _lib_path != _build.LIB_TRACE:
+            raise RuntimeError("the library is already loaded; choose the trace build first")
+        _lib_path = _build.build_trace()
+    return _lib_path
 
 
 def lib():
@@ -160,11 +176,12 @@ def lib():
     if _lib is None:
         with _lock:
             if _lib is None:
-                if not os.path.exists(_build.LIB):
+                path = _lib_path or _build.LIB
+                if not os.path.exists(path):
                     raise RuntimeError(
-                        "libaesoffload.so is not built; run paper_2607_02630_gb300.build.build() "
+                        f"{os.path.basename(path)} is not built; run paper_2607_02630_gb300.build.build() "
                         "(needs nvcc) -- there is no CPU fallback")
-                L = ctypes.CDLL(_build.LIB)
+                L = ctypes.CDLL(path)
                 for name, (res, args) in _SIGS.items():
                     f = getattr(L, name, None)
                     if f is None:
@@ -345,8 +362,10 @@ class Server:
     """Served mode: a resident kernel polling mapped descriptors (offload_*)."""
 
     def __init__(self, slots=0, max_keys=0, hbm_budget=0, ctas=0, threads=0, tile_blocks=0,
-                 idle_timeout_us=0, claim_mode=0):
-        cfg = ServerCfg(slots, max_keys, hbm_budget, ctas, threads, tile_blocks, idle_timeout_us, claim_mode)
+                 idle_timeout_us=0, claim_mode=0, trace_requests=0):
+        cfg = ServerCfg(slots, max_keys, hbm_budget, ctas, threads, tile_blocks, idle_timeout_us, claim_mode,
+                        trace_requests)
+        self.trace_requests = int(trace_requests)
         h = ctypes.c_void_p()
         _check(lib().offload_server_create(ctypes.byref(h), ctypes.byref(cfg)), "offload_server_create")
         self.handle = h.value
@@ -395,6 +414,21 @@ class Server:
 
     def wait(self, ticket: int, timeout_us: int = 5_000_000) -> int:
         return lib().offload_wait(self.handle, ctypes.c_uint64(ticket), ctypes.c_uint64(timeout_us))
+
+    TRACE_POINTS = ("dispatched", "published", "first_claim", "first_pop", "record_loaded", "keys_loaded",
+                    "first_tile_done", "done")
+
+    def trace(self):
+        """Trace builds: the stamp buffer as a uint64 array [trace_requests,
+        8] (ns; 0 = not reached); row s % trace_requests is request s
+        (sequence numbers count submits from 1)."""
+        import numpy as np
+
+        n = self.trace_requests * len(self.TRACE_POINTS)
+        out = np.zeros(n, dtype=np.uint64)
+        _check(lib().offload_server_trace(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n),
+               "offload_server_trace")
+        return out.reshape(self.trace_requests, len(self.TRACE_POINTS))
 
     def stats(self) -> dict:
         s = ServerStats()

@@ -19,6 +19,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaesoffload.so")
+# the trace build: served_protocol.cuh's stamps compiled in (-DSRV_TRACE);
+# only server.cu differs, the other objects are the normal build's
+LIB_TRACE = os.path.join(PKG, "libaesoffload_trace.so")
+BUILD_TRACE = os.path.join(PKG, "_build_trace")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -42,11 +46,40 @@ def _deps() -> list[str]:
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
+
+
+def _link(objs: list[str], lib: str) -> None:
+    nvcc = _nvcc()
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread", "-ldl", "-lrt"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, lib)
+
+
+def build_trace(force: bool = False) -> str:
+    """libaesoffload_trace.so: the library with the served kernel's
+    per-request stamps compiled in (offload_server_trace)."""
+    build()
+    if not force and not stale(LIB_TRACE):
+        return LIB_TRACE
+    os.makedirs(BUILD_TRACE, exist_ok=True)
+    srv = os.path.join(CSRC, "server.cu")
+    obj = os.path.join(BUILD_TRACE, "server.o")
+    r = subprocess.run([_nvcc()] + NVCC_FLAGS + ["-DSRV_TRACE", "-c", srv, "-o", obj], capture_output=True,
+                       text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on server.cu (trace build):\n{r.stdout}\n{r.stderr}")
+    objs = [obj if os.path.basename(s) == "server.cu" else
+            os.path.join(BUILD, os.path.splitext(os.path.basename(s))[0] + ".o") for s in sources()]
+    _link(objs, LIB_TRACE)
+    return LIB_TRACE
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -73,12 +106,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for s, log in zip(srcs, logs):
             sys.stderr.write(f"== {os.path.basename(s)}\n{log}")
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread", "-ldl", "-lrt"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    _link(objs, LIB)
     return LIB
 
 

@@ -102,6 +102,8 @@ struct SrvParams {
     const uint32_t *te0;
     uint32_t qmask, max_keys, tile_blocks, nslots;  // tile_blocks 0 = chosen per request
     uint64_t idle_ns, max_len;
+    unsigned long long *trace;  // trace builds: kTracePoints stamps per request (null: off)
+    uint32_t trace_mask;        // requests kept in the trace buffer - 1 (a power of two - 1)
 };
 
 // ---- memory operations ----------------------------------------------------
@@ -396,6 +398,31 @@ inline HostStats &host_stats()
 #define SRV_STAT(field) (::srvp::host_stats().field.fetch_add(1, std::memory_order_relaxed))
 #endif
 
+// ---- tracing (builds with -DSRV_TRACE) -------------------------------------
+// Per-request timer stamps of the protocol's steps, for latency breakdowns:
+// request seq's stamps sit at trace[(seq & trace_mask) * kTracePoints + point].
+// Other builds compile the stamps out, so the kernels are unchanged.
+enum TracePoint : uint32_t {
+    kTrDispatch = 0,    // a dispatcher has claimed the request (its order word seen)
+    kTrPublished,       // its record is complete and its ring entry about to be stored
+    kTrFirstClaim,      // an agent claimed its first tile (tile 0)
+    kTrFirstPop,        // a worker took tile 0 from its CTA's ring
+    kTrRecLoaded,       // that worker has the request's record
+    kTrKeysLoaded,      // that worker has its round keys in registers
+    kTrFirstTileDone,   // tile 0 is encrypted and stored
+    kTrDone,            // the last tile's worker raised the completion word
+    kTracePoints
+};
+#ifdef SRV_TRACE
+SRV_INLINE void trace(const SrvParams &p, uint32_t seq, uint32_t point)
+{
+    if (p.trace)
+        p.trace[(size_t)(seq & p.trace_mask) * kTracePoints + point] = gtime();
+}
+#else
+SRV_INLINE void trace(const SrvParams &, uint32_t, uint32_t) {}
+#endif
+
 // Nanoseconds since t0, as a signed count: a timer that steps back reads as
 // negative (not idle) instead of wrapping to a huge unsigned difference.
 SRV_INLINE int64_t since(uint64_t t0)
@@ -459,6 +486,8 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
     fence_acq_rel_sys();
     if (!PER_REQ && atom_cas(p.disp, (unsigned long long)k0, (unsigned long long)((k0 + m) & kSeqMask)) != k0)
         return 0;
+    for (uint32_t i = 0; i < m; ++i)
+        trace(p, (k0 + i) & kSeqMask, kTrDispatch);
     uint64_t x[kDispatchBatch][7];
 #pragma unroll
     for (uint32_t i = 0; i < kDispatchBatch; ++i) {
@@ -558,6 +587,8 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
         }
         fence_gpu();
     }
+    for (uint32_t i = 0; i < m; ++i)  // before the ring entries: no claim can precede it
+        trace(p, (k0 + i) & kSeqMask, kTrPublished);
 #pragma unroll
     for (uint32_t i = 0; i < kDispatchBatch; ++i)
         if (i < m)
@@ -567,6 +598,7 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
         if (i < m && done_word[i]) {
             const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
             fence_sys();
+            trace(p, (k0 + i) & kSeqMask, kTrDone);
             st_release_sys(p.done + d, (x[i][5] << 2) | done_word[i]);
         }
     }
@@ -652,6 +684,8 @@ SRV_FN uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &stop, 
                 *t1 = t + want < nt ? t + want : nt;
                 *nt_out = nt;
                 last_work = gtime();
+                if (t == 0)
+                    trace(p, seq, kTrFirstClaim);
                 return 0;
             }
         }
@@ -805,6 +839,8 @@ SRV_FN uint32_t claim_pr(const SrvParams &p, uint32_t &cur, uint64_t &last_work,
                     *t1 = t + want < nt ? (uint32_t)t + want : nt;
                     *nt_out = nt;
                     last_work = gtime();
+                    if (t == 0)
+                        trace(p, cur, kTrFirstClaim);
                     if (t + want >= nt) {  // took the request's last tiles
                         help_low(p, cur);
                         cur = (cur + 1) & kSeqMask;
@@ -829,6 +865,8 @@ SRV_FN uint32_t claim_pr(const SrvParams &p, uint32_t &cur, uint64_t &last_work,
                         *t1 = t + want < nt2 ? (uint32_t)t + want : nt2;
                         *nt_out = nt2;
                         last_work = gtime();
+                        if (t == 0)
+                            trace(p, vs, kTrFirstClaim);
                         SRV_STAT(recycled_claims);
                         return 0;
                     }
@@ -912,10 +950,12 @@ SRV_INLINE uint32_t lease_queued(const SrvParams &p, uint32_t cur, uint32_t lseq
 SRV_INLINE void tile_finished(const SrvParams &p, uint32_t d)
 {
     SrvRec *rec = p.recs + d;
-    const uint32_t ntiles = (uint32_t)(ld_relaxed_gpu(&rec->seq_ntiles) & kTileMask);
+    const uint64_t sn = ld_relaxed_gpu(&rec->seq_ntiles);
+    const uint32_t ntiles = (uint32_t)(sn & kTileMask);
     const unsigned int prev = atom_add(&rec->done_tiles, 1u);
     if (prev + 1 == ntiles) {
         fence_sys();
+        trace(p, (uint32_t)(sn >> kTileBits), kTrDone);
         st_release_sys(p.done + d, (ld_cg(&rec->gen) << 2) | 1u);
     }
 }

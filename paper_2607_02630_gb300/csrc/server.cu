@@ -96,12 +96,24 @@ struct RkRegsL2 {
 // Part `part` of `parts` of the single counter group [first, last) (or the
 // whole tile when parts == 1) of a request, done by the calling warp alone,
 // with the request's round keys in registers.
+// (stamp: trace builds record when the keys have arrived)
 template <int NR, int NB>
 __device__ __forceinline__ void run_part_regs(const aesrt::BatchReq &rq, uint64_t first, uint64_t last,
                                               uint32_t part, uint32_t parts, const uint8_t *smem,
-                                              const aestt::Lanes &ln)
+                                              const aestt::Lanes &ln, const SrvParams &p, uint32_t seq, bool stamp)
 {
     const RkRegsL2<NR> rk(rq.rk);
+#ifdef SRV_TRACE
+    if (stamp) {  // a move that reads the last round key waits for it, then the stamp
+        uint32_t sink;
+        asm volatile("mov.b32 %0, %1;" : "=r"(sink) : "r"(rk.get(NR).x));
+        trace(p, seq, kTrKeysLoaded);
+    }
+#else
+    (void)p;
+    (void)seq;
+    (void)stamp;
+#endif
     aestile::xor_range<NR, NB>(rq.in, rq.out, rq.len, rq.iv_hi, rq.iv_lo, first, last, part, parts, parts, smem,
                                ln, rk);
 }
@@ -142,6 +154,8 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
         d = __shfl_sync(0xffffffffu, d, 0);
         t = __shfl_sync(0xffffffffu, t, 0);
         seq = __shfl_sync(0xffffffffu, seq, 0);
+        if (lane == 0 && t == 0)
+            trace(p, seq, kTrFirstPop);
         SrvRec *rec = p.recs + d;
         if (d != cur_d || seq != cur_seq) {  // a new request for this warp: load it and its keys
             const uint4 *src = reinterpret_cast<const uint4 *>(&rec->rq);
@@ -152,6 +166,13 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
             tg = __ldcg(&rec->tile_groups);
             tp = __ldcg(&rec->tile_parts);
             __syncwarp();
+#ifdef SRV_TRACE
+            if (lane == 0 && t == 0) {  // a move that reads the record waits for it, then the stamp
+                uint64_t sink;
+                asm volatile("mov.b64 %0, %1;" : "=l"(sink) : "l"(rq.len));
+                trace(p, seq, kTrRecLoaded);
+            }
+#endif
             cur_d = d;
             cur_seq = seq;
         }
@@ -172,9 +193,9 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
             const uint32_t part = t % tp;
             aestile::tile_blocks_of(t / tp, tg, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first, &last);
             switch (rq.nr) {
-            case 10: run_part_regs<10, 2>(rq, first, last, part, tp, smem, ln); break;
-            case 12: run_part_regs<12, 2>(rq, first, last, part, tp, smem, ln); break;
-            default: run_part_regs<14, 2>(rq, first, last, part, tp, smem, ln); break;
+            case 10: run_part_regs<10, 2>(rq, first, last, part, tp, smem, ln, p, seq, lane == 0 && t == 0); break;
+            case 12: run_part_regs<12, 2>(rq, first, last, part, tp, smem, ln, p, seq, lane == 0 && t == 0); break;
+            default: run_part_regs<14, 2>(rq, first, last, part, tp, smem, ln, p, seq, lane == 0 && t == 0); break;
             }
         }
         // Order this lane's output stores before the tile is counted: at
@@ -185,6 +206,8 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
         else
             __threadfence();
         __syncwarp();
+        if (lane == 0 && t == 0)
+            trace(p, seq, kTrFirstTileDone);
         if (lane == 0)
             tile_finished(p, d);
     }
@@ -198,6 +221,8 @@ struct offload_server_s {
     int device = -1;
     int slots = 0, max_keys = 0, ctas = 0, threads = 0, tile_blocks = 0;
     int claim_mode = 0;  // 0: global cursor, 1: per-request claims
+    int trace_requests = 0;
+    unsigned long long *trace = nullptr;  // device stamp buffer (trace builds)
     uint32_t qsize = 0;
     uint64_t budget = 0, max_len = 0, idle_ns = 0;
     // mapped host memory
@@ -365,8 +390,13 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
         ctas > st->nsm || threads < 64 || threads > 32 * kMaxWarps || (threads & 31) ||
         !(tile_blocks == 0 || tile_blocks == 64 || tile_blocks == 128 ||
           (tile_blocks >= 256 && tile_blocks % 256 == 0)) ||
-        tile_blocks > (1 << 22) || c.claim_mode < 0 || c.claim_mode > 1)
+        tile_blocks > (1 << 22) || c.claim_mode < 0 || c.claim_mode > 1 || c.trace_requests < 0 ||
+        c.trace_requests > (1 << 20) || (c.trace_requests & (c.trace_requests - 1)))
         return AES_EINVAL;
+#ifndef SRV_TRACE
+    if (c.trace_requests)
+        return AES_EINVAL;  // this build has no stamps to record
+#endif
     offload_server_s *s = new (std::nothrow) offload_server_s();
     if (!s)
         return AES_ENOMEM;
@@ -377,6 +407,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     s->threads = threads;
     s->tile_blocks = tile_blocks;
     s->claim_mode = c.claim_mode;
+    s->trace_requests = c.trace_requests;
     s->budget = c.hbm_budget;
     s->idle_ns = 1000ull * (c.idle_timeout_us ? c.idle_timeout_us : 200000u);
     // tiles of at least 64 blocks (1024 adaptive for long requests) keep the tile count < kMaxTiles
@@ -404,6 +435,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
         if (s->setup)
             cudaStreamDestroy(s->setup);
         cudaFree(s->dmem);
+        cudaFree(s->trace);
         cudaFreeHost(s->queue);
         cudaFreeHost(s->order);
         cudaFreeHost(s->done);
@@ -458,6 +490,14 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     P.keys = reinterpret_cast<const uint4 *>(s->dmem + off_keys);
     P.key_nr = reinterpret_cast<const int *>(s->dmem + off_nr);
     s->key_stage = s->dmem + off_stage;
+    if (s->trace_requests) {
+        const size_t tb = sizeof(unsigned long long) * kTracePoints * (size_t)s->trace_requests;
+        if ((e = cudaMalloc(reinterpret_cast<void **>(&s->trace), tb)) ||
+            (e = cudaMemsetAsync(s->trace, 0, tb, s->setup)) || (e = cudaStreamSynchronize(s->setup)))
+            return fail("trace buffer");
+        P.trace = s->trace;
+        P.trace_mask = (uint32_t)s->trace_requests - 1;
+    }
     void *dp = nullptr;
     if ((e = cudaHostGetDevicePointer(&dp, s->queue, 0)))
         return fail("cudaHostGetDevicePointer");
@@ -635,6 +675,22 @@ int offload_wait(offload_server_t s, uint64_t ticket, uint64_t timeout_us)
     }
 }
 
+int offload_server_trace(offload_server_t s, uint64_t *out, size_t max_words)
+{
+    static_assert(kTracePoints == AES_TRACE_POINTS, "trace points");
+    if (!s || !out || !s->trace)
+        return AES_EINVAL;
+    size_t n = (size_t)kTracePoints * (size_t)s->trace_requests;
+    if (n > max_words)
+        n = max_words;
+    cudaError_t e = cudaMemcpyAsync(out, s->trace, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->setup);
+    if (!e)
+        e = cudaStreamSynchronize(s->setup);
+    if (e)
+        return cuda_fail(e, "offload_server_trace");
+    return (int)n;
+}
+
 int offload_server_stats(offload_server_t s, offload_stats_t *out)
 {
     if (!s || !out)
@@ -670,6 +726,7 @@ int offload_server_destroy(offload_server_t s)
     cudaStreamDestroy(s->stream);
     cudaStreamDestroy(s->setup);
     cudaFree(s->dmem);
+    cudaFree(s->trace);
     cudaFreeHost(s->queue);
     cudaFreeHost(s->order);
     cudaFreeHost(s->done);

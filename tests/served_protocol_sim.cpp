@@ -77,6 +77,7 @@ struct Sim {
     SrvParams P{};
 
     std::unique_ptr<Req[]> reqs;
+    std::vector<unsigned long long> tracebuf;  // SRV_TRACE builds: stamps of every request
     std::atomic<int> errors{0};
     std::mutex err_mu;
     char first_error[256] = "";
@@ -132,6 +133,36 @@ struct Sim {
         P.nslots = (uint32_t)slots;
         P.idle_ns = idle_ns;
         P.max_len = 1ull << 40;
+#ifdef SRV_TRACE
+        uint32_t tcap = 1;
+        while (tcap < (uint32_t)nreq + 2)
+            tcap <<= 1;
+        tracebuf.assign((size_t)tcap * kTracePoints, 0);
+        P.trace = tracebuf.data();
+        P.trace_mask = tcap - 1;
+#endif
+    }
+
+    // SRV_TRACE builds: every completed request's stamps come in protocol
+    // order (dispatched, published, first claim, first pop, done; a request
+    // without tiles: dispatched, published, done).
+    void check_trace()
+    {
+#ifdef SRV_TRACE
+        for (int i = 0; i < nreq && !errors.load(); ++i) {
+            const unsigned long long *row = &tracebuf[(size_t)((i + 1) & P.trace_mask) * kTracePoints];
+            const Req &r = reqs[(size_t)i];
+            if (r.ntiles) {
+                const uint32_t order[] = {kTrDispatch, kTrPublished, kTrFirstClaim, kTrFirstPop, kTrDone};
+                for (int k = 0; k < 5; ++k)
+                    if (!row[order[k]] || (k && row[order[k]] < row[order[k - 1]]))
+                        fail("seq %llu: stamp %llu missing or out of order", (uint64_t)i + 1, order[k]);
+            } else if (!row[kTrDispatch] || row[kTrPublished] < row[kTrDispatch] ||
+                       row[kTrDone] < row[kTrPublished] || row[kTrFirstClaim]) {
+                fail("seq %llu (no tiles): stamps out of order", (uint64_t)i + 1);
+            }
+        }
+#endif
     }
 
     // The tile count dispatch gives a request (restated here to size the
@@ -175,6 +206,8 @@ struct Sim {
             Tile tl{};
             if (!ring_pop(c->ring, &tl.d, &tl.t, &tl.seq))
                 break;
+            if (tl.t == 0)
+                trace(P, tl.seq, kTrFirstPop);
             process(tl);
             tile_finished(P, tl.d);
         }
@@ -365,6 +398,7 @@ struct Sim {
         }
         if (!errors.load() && tiles_done.load() != want_tiles)
             fail("%llu tiles processed, %llu expected", tiles_done.load(), want_tiles);
+        check_trace();
         const HostStats &hs = host_stats();
         std::printf("%s mode=%d ctas=%d slots=%d requests=%d completed=%d tiles=%llu launches=%d "
                     "stale_retries=%llu recycled=%llu repairs=%llu %s\n",

@@ -110,3 +110,26 @@ def test_with_weak_store_visibility(sim, mode, case):
     without its fence fails here)."""
     r = subprocess.run([sim, str(mode)] + [str(x) for x in case], capture_output=True, text=True, timeout=240)
     assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
+
+
+@pytest.fixture(scope="module")
+def sim_trace(tmp_path_factory):
+    """The simulation with the protocol's trace stamps compiled in (-DSRV_TRACE)."""
+    nvcc = B._nvcc()
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+    exe = str(tmp_path_factory.mktemp("simtr") / "served_protocol_sim_trace")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", "-Wall", "-Wno-unknown-pragmas", "-DSRV_TRACE",
+                    "-fsanitize=undefined", "-fno-sanitize-recover=undefined", "-I", B.INCLUDE, "-I", B.CSRC,
+                    "-I", cuda_inc, os.path.join(HERE, "served_protocol_sim.cpp"), "-o", exe], check=True)
+    return exe
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["global_cursor", "per_request"])
+@pytest.mark.parametrize("case", [(8, 8, 1500, 0, 2000, 5, 0, 2, 0), (4, 2, 1000, 64, 2000, 6, 0, 3, 1)],
+                         ids=["plain", "weak"])
+def test_trace_stamps_follow_the_protocol(sim_trace, mode, case):
+    """Every request's trace stamps come in protocol order: dispatched,
+    published, first claim, first pop, done (without tiles: dispatched,
+    published, done)."""
+    r = subprocess.run([sim_trace, str(mode)] + [str(x) for x in case], capture_output=True, text=True, timeout=240)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr

@@ -660,3 +660,17 @@ def test_served_every_length_0_to_64(cuda, aes, ncpu, bits):
             assert (out[o + n: o + n + 16] == 0xA5).all(), f"bytes past len {n} were written"
     finally:
         assert srv.close() == aes.AES_OK
+
+
+def test_trace_build_stamps(cuda, aes):
+    """The trace build (libaesoffload_trace.so, built here) stamps each served
+    request's steps, in protocol order; run in a child process, which loads
+    that library instead of the normal one."""
+    import os
+    import subprocess
+    import sys
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([sys.executable, os.path.join(here, "trace_gpu_child.py")], capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and "OK " in r.stdout, r.stdout + r.stderr
