@@ -681,6 +681,21 @@ def conflict_study(args, rank, local):
     return 0
 
 
+def served_trace(args, rank):
+    """The trace build's step breakdown of one-in-flight served latency
+    (paper_2607_02630_gb300.served_trace), in a child process: it loads
+    libaesoffload_trace.so, which this process must not have loaded."""
+    if rank != 0:
+        return 0
+    root = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([sys.executable, "-m", "paper_2607_02630_gb300.served_trace", "--requests",
+                        str(args.served_trace_requests), "--claim-mode", str(args.claim_mode)],
+                       capture_output=True, text=True, cwd=root)
+    sys.stdout.write(r.stdout)
+    sys.stderr.write(r.stderr)
+    return r.returncode
+
+
 # ----------------------------------------------------------------------- our arm
 
 def main():
@@ -724,6 +739,9 @@ def main():
     ap.add_argument("--served-requests", type=int, default=20000)
     ap.add_argument("--claim-mode", type=int, default=0, choices=[0, 1],
                     help="served studies: 0 = global claim cursor, 1 = per-request claim words")
+    ap.add_argument("--served-trace", action="store_true",
+                    help="served one-in-flight latency breakdown from the trace build (its own process)")
+    ap.add_argument("--served-trace-requests", type=int, default=500)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -738,6 +756,8 @@ def main():
         return conflict_study(args, rank, local)
     if args.served:
         return served(args, rank, local)
+    if args.served_trace:
+        return served_trace(args, rank)
 
     import torch
 

@@ -664,13 +664,17 @@ def test_served_every_length_0_to_64(cuda, aes, ncpu, bits):
 
 def test_trace_build_stamps(cuda, aes):
     """The trace build (libaesoffload_trace.so, built here) stamps each served
-    request's steps, in protocol order; run in a child process, which loads
-    that library instead of the normal one."""
+    request's steps, in protocol order.  Run as its own process
+    (paper_2607_02630_gb300.served_trace), which loads that library instead
+    of the normal one."""
+    import json
     import os
     import subprocess
     import sys
 
-    here = os.path.dirname(os.path.abspath(__file__))
-    r = subprocess.run([sys.executable, os.path.join(here, "trace_gpu_child.py")], capture_output=True, text=True,
-                       timeout=600)
-    assert r.returncode == 0 and "OK " in r.stdout, r.stdout + r.stderr
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-m", "paper_2607_02630_gb300.served_trace", "--requests", "40"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stdout + r.stderr
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    assert res["ordered"] and res["median_us"]["done"] > 0, res
