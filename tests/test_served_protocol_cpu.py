@@ -133,3 +133,24 @@ def test_trace_stamps_follow_the_protocol(sim_trace, mode, case):
     published, done)."""
     r = subprocess.run([sim_trace, str(mode)] + [str(x) for x in case], capture_output=True, text=True, timeout=240)
     assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
+
+
+def soak_case(seed: int):
+    """A configuration drawn from the seed: CTAs, slots, tile shape, idle
+    timeout, scenario, perturbation and weak stores (reproducible)."""
+    ctas = seed * 7 % 15 + 1
+    slots = 1 << (seed % 7)
+    tile_blocks = (0, 64, 256, 1024)[seed % 4]
+    scenario = 1 if seed % 11 == 0 else (2 if seed % 13 == 0 else 0)
+    idle_us = 400 if seed % 2 == 0 else 3000
+    return [ctas, slots, 600, tile_blocks, idle_us, seed, scenario, seed % 5, (seed // 3) % 2]
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["global_cursor", "per_request"])
+@pytest.mark.parametrize("seed", list(range(2000, 2024)))
+def test_randomised_configurations(sim_trace, mode, seed):
+    """Configurations drawn from seeds across every switch of the simulation
+    (the trace build, so stamp order is checked too)."""
+    r = subprocess.run([sim_trace, str(mode)] + [str(x) for x in soak_case(seed)], capture_output=True, text=True,
+                       timeout=240)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
