@@ -163,3 +163,12 @@ def test_short_keys_are_refused_before_the_library_reads_them():
         A._keybuf(bytes(23), 192)
     assert A._keybuf(bytes(32), 256) == bytes(32)
     assert A._keybuf(b"x", 64) == b"x"  # a key size the library rejects itself (AES_EKEYBITS)
+
+
+def test_trace_build_builds_and_exports_its_reader():
+    """The served path's trace build (-DSRV_TRACE) compiles, links, and
+    exports offload_server_trace like the normal library."""
+    path = B.build_trace()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert "offload_server_trace" in exported and "offload_submit" in exported
