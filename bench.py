@@ -163,6 +163,27 @@ def ttable_lookups(w) -> int:
     return total
 
 
+def bitslice_ops(w) -> float:
+    """Logic ops the bitsliced method needs for workload w: per 32 blocks
+    (one thread's planes) 16 S-box circuits of 113 gates per round,
+    MixColumns' 416 xors per full round and 128 key xors per round key."""
+    total = 0.0
+    for n, b in zip(w.lengths, w.bits):
+        nb = (int(n) + 15) // 16
+        nr = int(b) // 32 + 6
+        total += nb * (16 * 113 * nr + 416 * (nr - 1) + 128 * (nr + 1)) / 32.0
+    return total
+
+
+def measured_rates(A):
+    """aes_measure_peaks on this GPU (per-SM issue rates from clock64, link
+    bandwidths from CUDA events); None if the probe fails."""
+    try:
+        return A.measure_peaks()
+    except Exception as e:  # reported, not fatal: the roofline then says so
+        return {"error": str(e)}
+
+
 # --------------------------------------------------------------------- oracle leg
 
 def oracle_sample(w, budget_s: float, nthreads: int):
@@ -681,6 +702,30 @@ def conflict_study(args, rank, local):
     return 0
 
 
+def peaks_mode(local):
+    """The roofline's denominators, regenerated on this GPU: per-SM issue
+    rates (clock64) and host-link bandwidths (CUDA events)."""
+    import torch
+
+    from paper_2607_02630_gb300 import aesoffload as A
+    from paper_2607_02630_gb300 import build as libbuild
+
+    torch.cuda.set_device(local)
+    libbuild.build()
+    r = A.measure_peaks()
+    pk, pk_kind = peaks()
+    f = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    nsm = r["sms"]
+    out = {"metric": "device rates behind the AES-CTR roofline", "rates": r,
+           "derived": {"ttable_lookups_per_s_at_max_clock": r["lds32_per_clk_sm"] * nsm * f,
+                       "lop3_per_s_at_max_clock": r["lop3_per_clk_sm"] * nsm * f,
+                       "sm_max_mhz": f / 1e6, "sm_max_mhz_source": pk_kind},
+           "how": "aes_measure_peaks: 2 CTAs x 1024 threads per SM, 8 independent chains a thread, "
+                  "clock64 per SM (median over SMs); 256 MiB transfers timed with CUDA events"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def served_trace(args, rank):
     """The trace build's step breakdown of one-in-flight served latency
     (paper_2607_02630_gb300.served_trace), in a child process: it loads
@@ -742,6 +787,11 @@ def main():
     ap.add_argument("--served-trace", action="store_true",
                     help="served one-in-flight latency breakdown from the trace build (its own process)")
     ap.add_argument("--served-trace-requests", type=int, default=500)
+    ap.add_argument("--batch-shape", default=None,
+                    help="variant,threads,tile_blocks,blocks_per_thread: time this batch shape instead of the "
+                         "autotuner's pick (profiler captures of the pick)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the roofline's device rates (aes_measure_peaks) as one JSON line and exit")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -758,6 +808,8 @@ def main():
         return served(args, rank, local)
     if args.served_trace:
         return served_trace(args, rank)
+    if args.peaks:
+        return peaks_mode(local)
 
     import torch
 
@@ -783,7 +835,17 @@ def main():
     ctxs = [A.Context(w.key_of(i).tobytes(), int(w.bits[i])) for i in range(w.n)]
     reqs = [(ctxs[i], w.ivs[i].tobytes(), src.data_ptr() + int(w.offsets[i]),
              dst.data_ptr() + int(w.offsets[i]), int(w.lengths[i])) for i in range(w.n)]
-    plan = A.BatchPlan(reqs)
+    # the device's rates behind the roofline, then the batch autotuner on
+    # these very requests (every candidate shape timed as a graph plan); the
+    # plan below uses the shape it picks
+    rates = measured_rates(A)
+    if args.batch_shape:  # a fixed shape (profiler captures): no tuning
+        v, th, tb, nb = (int(x) for x in args.batch_shape.split(","))
+        tuned = {"variant": v, "threads": th, "tile_blocks": tb, "ctas": 0, "blocks_per_thread": nb}
+        plan = A.BatchPlan(reqs, variant=v, threads=th, tile_blocks=tb, blocks_per_thread=nb)
+    else:
+        tuned = A.batch_autotune(reqs, sh)
+        plan = A.BatchPlan(reqs)
     step_bytes = plan.nbytes
     torch.cuda.synchronize()
 
@@ -814,27 +876,10 @@ def main():
     value = R.aggregate_gbs(step_bytes, args.steps, ws, elapsed)
     clocks = clk.summary()
 
-    # ---- roofline of the batch kernel (on-chip shared-memory lookup bound)
-    pk, pk_kind = peaks()
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    lookups = ttable_lookups(w)
-    lookups_per_s_peak = 32.0 * nsm * sm_max_mhz * 1e6  # one 128-byte shared-memory wavefront / clk / SM
-    floor_s = lookups / lookups_per_s_peak
-    roof_gbs = step_bytes / floor_s / 1e9
-    launch_s = statistics.mean(per_launch)
-    achieved = step_bytes / launch_s / 1e9
-    hbm_roof = float(pk.get("hbm_gbs", 6784.5)) / 2.0  # 2 bytes moved per payload byte
-    roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(roof_gbs, 2), "unit": "GB/s",
-                "frac": round(achieved / roof_gbs, 4), "traffic": None,
-                "peak_basis": f"T-table lookups at one 128-byte shared-memory wavefront (32 lookups) per clk "
-                              f"per SM x {nsm} SMs x {sm_max_mhz:.0f} MHz ({pk_kind} max clock); "
-                              f"{lookups / 1e9:.3f} G lookups per step (16*Nr per block, rounds 1-2 "
-                              f"counter-cached: 5 per block + 27 per 256-block counter group)",
-                "hbm_payload_roof_gbs": round(hbm_roof, 1),
-                "frac_of_hbm_roof": round(achieved / hbm_roof, 4),
-                "kernel": "batch_ttable_kernel"}
-    roofline["traffic"] = captured_traffic(step_bytes)
+    # ---- roofline of the batch kernel (on-chip bound: shared-memory lookups
+    # for the T-tables, logic issue for the bitsliced circuit), from the
+    # rates aes_measure_peaks measured on this GPU
+    roofline = batch_roofline(torch, dev, w, step_bytes, per_launch, tuned, rates)
 
     extras = {}
     if not args.no_extras:
@@ -842,6 +887,14 @@ def main():
 
     # ---- end to end: payloads in pinned host memory, read/written by the kernel over C2C
     e2e = None if args.no_e2e else run_e2e(A, torch, w, ctxs, args, sh, stream, dist, ws)
+    if e2e is not None and rates.get("zero_copy_each_way_gbs"):
+        link = rates["zero_copy_each_way_gbs"]
+        e2e["link_roof_gbs"] = round(link, 1)
+        e2e["frac_of_link_roof"] = round(e2e["value"] / link, 4)
+        e2e["link_roof_basis"] = ("aes_measure_peaks: a kernel reading 256 MiB of pinned host memory and writing "
+                                  "256 MiB of pinned host memory at once over NVLink-C2C, per direction "
+                                  f"(copy engines: {rates['h2d_gbs']:.1f} H2D, {rates['d2h_gbs']:.1f} D2H, "
+                                  f"{rates['h2d_d2h_each_way_gbs']:.1f} each way at once)")
 
     if rank == 0:
         cpu = None
@@ -862,7 +915,13 @@ def main():
                        "global_batch": args.requests * ws, "seq_len": None,
                        "parallelism": f"replicas{ws}", "step_bytes": step_bytes,
                        "l2": "no flush: 3.8 GB of inputs per step, far above the 129 MB L2",
-                       "launch": "aes_batch_plan_launch (CUDA graph: counter reset + persistent kernel)"},
+                       "launch": "aes_batch_plan_launch (CUDA graph: counter reset + persistent kernel)",
+                       "tuned_shape": tuned,
+                       "tuner": ("fixed by --batch-shape" if args.batch_shape else
+                                 "aes_batch_autotune on these requests before the timed region: 30 shapes "
+                                 "(T-table CTAs of 256/512/1024 threads x 1/2/4 blocks per lane x tiles of "
+                                 "1024/2048/4096 blocks, and the bitsliced kernel x the 3 tiles), median of 5 "
+                                 "graph launches each")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -875,6 +934,45 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def batch_roofline(torch, dev, w, step_bytes, per_launch, tuned, rates):
+    """The dominant kernel's roofline: achieved payload GB/s per launch
+    against the on-chip floor of the variant the tuner picked."""
+    pk, pk_kind = peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    launch_s = statistics.mean(per_launch)
+    achieved = step_bytes / launch_s / 1e9
+    hbm_roof = float(pk.get("hbm_gbs", 6784.5)) / 2.0  # 2 bytes moved per payload byte
+    bitsliced = tuned.get("variant") == 2
+    measured = "lds32_per_clk_sm" in rates
+    if bitsliced:
+        work = bitslice_ops(w)
+        per_clk = rates["lop3_per_clk_sm"] if measured else 64.0
+        what = (f"{work / 1e9:.3f} G logic ops per step (per 32 blocks: 16 S-box circuits of 113 gates per round, "
+                f"416 MixColumns xors per full round, 128 key xors per round key) at {per_clk:.1f} lop3 lanes per "
+                f"clk per SM")
+        kernel = "batch_bitslice_kernel"
+    else:
+        work = ttable_lookups(w)
+        per_clk = rates["lds32_per_clk_sm"] if measured else 32.0
+        what = (f"{work / 1e9:.3f} G T-table lookups per step (16*Nr per block, rounds 1-2 counter-cached: 5 per "
+                f"block + 27 per 256-block counter group) at {per_clk:.2f} conflict-free 32-bit shared-memory "
+                f"loads per clk per SM")
+        kernel = "batch_ttable_kernel"
+    src = ("measured on this GPU by aes_measure_peaks (clock64 per SM)" if measured
+           else f"nominal rate: aes_measure_peaks failed ({rates.get('error')})")
+    floor_s = work / (per_clk * nsm * sm_max_mhz * 1e6)
+    roof_gbs = step_bytes / floor_s / 1e9
+    return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(roof_gbs, 2), "unit": "GB/s",
+            "frac": round(achieved / roof_gbs, 4),
+            "traffic": captured_traffic(step_bytes) if not bitsliced else None,
+            "peak_basis": f"{what} ({src}) x {nsm} SMs x {sm_max_mhz:.0f} MHz ({pk_kind} max clock)",
+            "rates": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in rates.items()},
+            "hbm_payload_roof_gbs": round(hbm_roof, 1),
+            "frac_of_hbm_roof": round(achieved / hbm_roof, 4),
+            "kernel": kernel}
 
 
 def run_extras(A, torch, dev, stream, sh, w, ctxs, reqs, src, dst, step_bytes, args):

@@ -147,15 +147,20 @@ typedef struct {
 
 /* Options of the persistent batch kernel (all-zero = tuned defaults). */
 typedef struct {
-    int variant;        /* AES_VARIANT_* (AUTO picks T-table) */
+    int variant;        /* AES_VARIANT_* (AUTO: the tuned variant, T-table
+                           until aes_batch_autotune picks otherwise) */
     int threads;        /* CTA size, multiple of 32, 32..1024 (default 512): up
                            to 512 the warps keep round keys in registers,
-                           above it in shared memory */
+                           above it in shared memory; the bitsliced kernel
+                           takes 128 only */
     int tile_blocks;    /* 16-byte blocks per work tile: a multiple of 256 (whole counter groups) */
     int ctas;           /* persistent CTAs; 0 = one per SM (x occupancy) */
     uint32_t tile_order_seed; /* nonzero: tiles are claimed in a seeded
                                  pseudo-random permutation (testing aid; the
                                  result must not change) */
+    int blocks_per_thread; /* T-table: 16-byte blocks each lane keeps in flight
+                              (1, 2 or 4); ignored by the bitsliced kernel,
+                              which always holds 32 per lane */
 } aes_batch_opts_t;
 
 /* Encrypt n independent requests in ONE persistent-kernel launch on
@@ -181,12 +186,19 @@ int aes_ctr_batch_ex(const aes_desc_t *descs, int n, void *stream, const aes_bat
  * (about 64 KiB) that every GPU loading the library keeps until exit.  The
  * key contexts must already exist on the current device (AES_EINVAL if no
  * context was ever created on it).  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call reuses the same array and leaves
- * its contents behind: calls whose work may overlap on the GPU (other
- * streams, other threads) race on it and must be serialised by the caller.
- * Errors: those of aes_ctr_batch, and AES_ETOOBIG when n exceeds
- * AES_NOALLOC_MAX_REQUESTS. */
+ * the array's device address (cudaGetSymbolAddress) and keeps it.  Every
+ * call copies its descriptors into the array with cudaMemcpyAsync from
+ * pageable host memory, so no call -- the first or a later one -- may be
+ * made while `stream` is being captured into a CUDA graph (the capture
+ * would refuse the copy); callers that need a graph use the batch plans
+ * (aes_batch_plan_create), which allocate once, up front.  Every call reuses
+ * the same array and leaves its contents behind: calls whose work may
+ * overlap on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller.  The kernel is the T-table batch kernel in the
+ * device's tuned T-table shape (tiles of whole counter groups, claimed by
+ * each warp), finding each tile's request by a binary search in shared
+ * memory instead of a tile map.  Errors: those of aes_ctr_batch, and
+ * AES_ETOOBIG when n exceeds AES_NOALLOC_MAX_REQUESTS. */
 #define AES_NOALLOC_MAX_REQUESTS 1024
 int aes_ctr_batch_noalloc(const aes_desc_t *descs, int n, void *stream);
 
@@ -216,8 +228,60 @@ int aes_autotune(const char *path);
  * device with another name or SM count).  AES_EINVAL if unreadable. */
 int aes_autotune_load(const char *path);
 
+/* Tune the batch kernel on the caller's own requests (the batching pattern's
+ * autotuner): every candidate shape -- variant (T-table or bitsliced), CTA
+ * size, blocks per lane in flight and tile size -- is built as a plan over
+ * descs[0..n) and timed with CUDA events on `stream` (median of 5 launches
+ * after 2 warm-ups); the fastest becomes the device's shape for
+ * AES_VARIANT_AUTO batches and plans, and is returned in *best (may be
+ * NULL).  Every candidate encrypts the requests several times, so their
+ * outputs are overwritten (with the correct ciphertext: each launch computes
+ * out = in xor keystream).  Requests must not be in place (in == out) if the
+ * input has to survive.  Synchronous; allocates; not for use inside stream
+ * capture.  Errors: those of aes_batch_plan_create, AES_ECUDA. */
+int aes_batch_autotune(const aes_desc_t *descs, int n, void *stream, aes_batch_opts_t *best);
+
+/* The batch shape AES_VARIANT_AUTO uses on the current device (the default,
+ * or the last aes_batch_autotune / aes_autotune / aes_autotune_load). */
+int aes_batch_tuned_shape(aes_batch_opts_t *out);
+
 /* Describe the shape AES_VARIANT_AUTO picks for (len, bits). */
 int aes_tuned_shape(size_t len, int bits, aes_launch_t *out);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Device rates behind the benchmark's roofline (this call computes no AES;
+ * the paper has no counterpart: it reports no device-side rates).  Per-SM
+ * rates come from clock64() on each SM (median over SMs of operations per
+ * SM clock, 2 CTAs of 1024 threads per SM, 8 independent chains a thread);
+ * link bandwidths from CUDA events over 256 MiB transfers (median of 3).
+ *   lds32_per_clk_sm        conflict-free 32-bit shared-memory loads (lane l
+ *                           reads bank l; the T-table lookup pattern)
+ *   lop3_per_clk_sm         three-input logic ops (lop3.b32)
+ *   prmt_per_clk_sm         byte permutes (prmt.b32)
+ *   iadd_per_clk_sm         32-bit adds
+ *   sm_mhz_during_probe     SM cycles / event time of the load probe
+ *   h2d_gbs, d2h_gbs        copy engine, pinned host memory, one direction
+ *   h2d_d2h_each_way_gbs    both directions at once, per direction
+ *   zero_copy_each_way_gbs  a kernel reading pinned host memory and writing
+ *                           pinned host memory at once (NVLink-C2C), per
+ *                           direction: the end-to-end path's link bound
+ * Synchronous; allocates and frees its buffers (512 MiB pinned host memory,
+ * 512 MiB device memory).  Errors: AES_EINVAL (NULL out), AES_ENOMEM,
+ * AES_ECUDA. */
+typedef struct {
+    int sms;
+    double lds32_per_clk_sm;
+    double lop3_per_clk_sm;
+    double prmt_per_clk_sm;
+    double iadd_per_clk_sm;
+    double sm_mhz_during_probe;
+    double h2d_gbs;
+    double d2h_gbs;
+    double h2d_d2h_each_way_gbs;
+    double zero_copy_each_way_gbs;
+} aes_peaks_t;
+int aes_measure_peaks(aes_peaks_t *out);
 
 /* ---------------------------------------------------------------- served mode */
 
@@ -391,7 +455,8 @@ int offload_drive_ex(offload_server_t srv, const aes_drive_req_t *reqs, int n, i
 /* Per-call path with the same schedule: each thread owns a CUDA stream,
  * launches aes_ctr, records an event and polls it with cudaEventQuery (the
  * paper's completion mechanism, Sec. 6 setup); at most 256 requests in
- * flight per thread. */
+ * flight per thread.  Events on one stream complete in order, so a thread
+ * queries only its oldest pending event on each pass. */
 int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, int n, int nthreads,
                   double *latency_us, aes_drive_result_t *res);
 

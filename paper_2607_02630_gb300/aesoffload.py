@@ -59,7 +59,14 @@ class Desc(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("threads", ctypes.c_int), ("tile_blocks", ctypes.c_int),
-                ("ctas", ctypes.c_int), ("tile_order_seed", ctypes.c_uint32)]
+                ("ctas", ctypes.c_int), ("tile_order_seed", ctypes.c_uint32), ("blocks_per_thread", ctypes.c_int)]
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int), ("lds32_per_clk_sm", ctypes.c_double), ("lop3_per_clk_sm", ctypes.c_double),
+                ("prmt_per_clk_sm", ctypes.c_double), ("iadd_per_clk_sm", ctypes.c_double),
+                ("sm_mhz_during_probe", ctypes.c_double), ("h2d_gbs", ctypes.c_double), ("d2h_gbs", ctypes.c_double),
+                ("h2d_d2h_each_way_gbs", ctypes.c_double), ("zero_copy_each_way_gbs", ctypes.c_double)]
 
 
 class ServerCfg(ctypes.Structure):
@@ -128,6 +135,11 @@ _SIGS = {
     "aes_autotune": (ctypes.c_int, [ctypes.c_char_p]),
     "aes_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "aes_tuned_shape": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(LaunchShape)]),
+    "aes_batch_autotune": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(BatchOpts)]),
+    "aes_batch_tuned_shape": (ctypes.c_int, [ctypes.POINTER(BatchOpts)]),
+    "aes_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks)]),
+    "aes_ctr_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int, ctypes.c_void_p]),
     "offload_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ServerCfg)]),
     "offload_key_register": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]),
@@ -302,10 +314,16 @@ def _descs(requests):
 
 
 def batch_status(requests, stream=None, variant=0, threads=0, tile_blocks=0, ctas=0,
-                 tile_order_seed=0) -> int:
+                 tile_order_seed=0, blocks_per_thread=0) -> int:
     arr = _descs(requests)
-    opts = BatchOpts(variant, threads, tile_blocks, ctas, tile_order_seed)
+    opts = BatchOpts(variant, threads, tile_blocks, ctas, tile_order_seed, blocks_per_thread)
     return lib().aes_ctr_batch_ex(arr, len(requests), stream_handle(stream), ctypes.byref(opts))
+
+
+def batch_noalloc_status(requests, stream=None) -> int:
+    """aes_ctr_batch_noalloc (no device allocation; at most 1024 requests)."""
+    arr = _descs(requests)
+    return lib().aes_ctr_batch_noalloc(arr, len(requests), stream_handle(stream))
 
 
 def batch(requests, stream=None, **opts) -> None:
@@ -316,9 +334,10 @@ def batch(requests, stream=None, **opts) -> None:
 class BatchPlan:
     """aes_batch_plan_*: a device-resident descriptor table + captured CUDA graph."""
 
-    def __init__(self, requests, variant=0, threads=0, tile_blocks=0, ctas=0, tile_order_seed=0):
+    def __init__(self, requests, variant=0, threads=0, tile_blocks=0, ctas=0, tile_order_seed=0,
+                 blocks_per_thread=0):
         arr = _descs(requests)
-        opts = BatchOpts(variant, threads, tile_blocks, ctas, tile_order_seed)
+        opts = BatchOpts(variant, threads, tile_blocks, ctas, tile_order_seed, blocks_per_thread)
         h = ctypes.c_void_p()
         _check(lib().aes_batch_plan_create(ctypes.byref(h), arr, len(requests), ctypes.byref(opts)),
                "aes_batch_plan_create")
@@ -349,6 +368,34 @@ def autotune(path: str | None = None) -> None:
 
 def autotune_load(path: str) -> None:
     _check(lib().aes_autotune_load(path.encode()), "aes_autotune_load")
+
+
+def _batch_opts_dict(o: BatchOpts) -> dict:
+    return {"variant": o.variant, "threads": o.threads, "tile_blocks": o.tile_blocks, "ctas": o.ctas,
+            "blocks_per_thread": o.blocks_per_thread}
+
+
+def batch_autotune(requests, stream=None) -> dict:
+    """aes_batch_autotune: time every batch shape on these requests (their
+    outputs are overwritten) and make the fastest the device's batch shape."""
+    arr = _descs(requests)
+    best = BatchOpts()
+    _check(lib().aes_batch_autotune(arr, len(requests), stream_handle(stream), ctypes.byref(best)),
+           "aes_batch_autotune")
+    return _batch_opts_dict(best)
+
+
+def batch_tuned_shape() -> dict:
+    o = BatchOpts()
+    _check(lib().aes_batch_tuned_shape(ctypes.byref(o)), "aes_batch_tuned_shape")
+    return _batch_opts_dict(o)
+
+
+def measure_peaks() -> dict:
+    """aes_measure_peaks: per-SM issue rates and host-link bandwidths."""
+    p = Peaks()
+    _check(lib().aes_measure_peaks(ctypes.byref(p)), "aes_measure_peaks")
+    return {name: getattr(p, name) for name, _ in Peaks._fields_}
 
 
 def tuned_shape(nbytes: int, bits: int) -> dict:

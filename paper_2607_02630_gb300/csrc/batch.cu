@@ -14,6 +14,11 @@
 // serves T-table lookups only; larger CTAs stage it in each warp's slice of
 // shared memory (one broadcast wavefront per round, about 5% of the pipe).
 //
+// The bitsliced kernel takes the same tiles with one warp per tile, 1024
+// blocks at a time, as the autotuner's alternative to the T-tables.  A search
+// variant of the T-table kernel finds a tile's request by binary search over
+// the requests' first tiles instead of a tile map (aes_ctr_batch_noalloc).
+//
 // A nonzero `order` enables a test aid: tile t is processed as tile
 // (a*t + b) mod T for a host-chosen a coprime to T (a permutation), so tiles
 // complete in a scrambled order; results must not change.
@@ -22,6 +27,7 @@
 #include "runtime.h"
 #include "common.cuh"
 #include "aes_ttable.cuh"
+#include "bs_tile.cuh"
 #include "tile.cuh"
 
 #include <algorithm>
@@ -39,32 +45,71 @@ struct TileOrder {
 
 // CTA sizes up to this hold round keys in registers.
 constexpr int kRegsMaxThreads = 512;
+// The bitsliced batch kernel's CTA size (its warps are register-bound).
+constexpr int kBsThreads = 128;
 
-template <int NB, int MAXT, bool RK_REGS>
+// The warp's next tile: lane 0 claims it from the device counter; returns
+// the tile index (>= total_tiles when none are left), permuted if asked.
+__device__ __forceinline__ unsigned long long claim_tile(unsigned long long *counter, uint64_t total_tiles,
+                                                         const TileOrder &order)
+{
+    unsigned long long t = 0;
+    if ((threadIdx.x & 31u) == 0)
+        t = atomicAdd(counter, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t < total_tiles && (order.a != 1 || order.b != 0))
+        t = (order.a * t + order.b) % total_tiles;
+    return t;
+}
+
+// Owner of tile t: the last request whose first tile is <= t (requests
+// without tiles share their first tile number with the next request and are
+// never chosen).  Lane 0 searches `begin[0..n)` in shared memory.
+__device__ __forceinline__ uint32_t owner_of(const uint64_t *begin, int n, unsigned long long t)
+{
+    int lo = 0;
+    if ((threadIdx.x & 31u) == 0) {
+        int hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (begin[mid] <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+    }
+    return (uint32_t)__shfl_sync(0xffffffffu, lo, 0);
+}
+
+// The persistent T-table batch kernel.  NB: blocks per lane in flight;
+// MAXT: largest CTA it is launched with; RK_REGS: round keys in registers
+// (else in the warp's slice of shared memory); SEARCH: tile owners found by
+// binary search over the requests' first tiles (copied into shared memory
+// behind the tables) instead of read from the tile map.
+template <int NB, int MAXT, bool RK_REGS, bool SEARCH>
 __global__ void __launch_bounds__(MAXT, 1)
-    batch_ttable_kernel(const BatchReq *__restrict__ reqs, const uint32_t *__restrict__ tile_req,
+    batch_ttable_kernel(const BatchReq *__restrict__ reqs, const uint32_t *__restrict__ tile_req, int nreq,
                         uint64_t total_tiles, unsigned long long *__restrict__ counter,
                         const uint32_t *__restrict__ te0, uint32_t tile_groups, TileOrder order)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint4 s_rk[RK_REGS ? 1 : MAXT / 32][15];  // round keys of each warp's current tile
+    uint64_t *s_begin = reinterpret_cast<uint64_t *>(smem + aestt::kTableBytes);
+    if (SEARCH)
+        for (int i = threadIdx.x; i < nreq; i += blockDim.x)
+            s_begin[i] = reqs[i].tile_begin;
     aestt::fill_tables(smem, te0);
     __syncthreads();
     const aestt::Lanes ln;
     const uint32_t lane = threadIdx.x & 31u;
     uint4 *w_rk = s_rk[RK_REGS ? 0 : threadIdx.x >> 5];
-    const bool permuted = order.a != 1 || order.b != 0;
     // Every warp claims tiles on its own: no CTA-wide barrier per tile.
     for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0)
-            t = atomicAdd(counter, 1ull);
-        t = __shfl_sync(0xffffffffu, t, 0);
+        const unsigned long long t = claim_tile(counter, total_tiles, order);
         if (t >= total_tiles)
             break;
-        if (permuted)
-            t = (order.a * t + order.b) % total_tiles;
-        const BatchReq rq = reqs[__ldg(tile_req + t)];
+        const uint32_t ri = SEARCH ? owner_of(s_begin, nreq, t) : __ldg(tile_req + t);
+        const BatchReq rq = reqs[ri];
         uint64_t first, last;
         aestile::tile_blocks_of(t - rq.tile_begin, tile_groups, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first,
                                 &last);
@@ -88,22 +133,129 @@ __global__ void __launch_bounds__(MAXT, 1)
     }
 }
 
+// The persistent bitsliced batch kernel: the same tiles and claims, each
+// tile encrypted by one warp 1024 blocks at a time (bs_tile.cuh) with the
+// request's round-key bit planes in the warp's slice of shared memory
+// (rebuilt when the warp moves to a request with another key).
+__global__ void __launch_bounds__(kBsThreads)
+    batch_bitslice_kernel(const BatchReq *__restrict__ reqs, const uint32_t *__restrict__ tile_req,
+                          uint64_t total_tiles, unsigned long long *__restrict__ counter, uint32_t tile_groups,
+                          TileOrder order)
+{
+    __shared__ __align__(16) uint32_t s_mask[kBsThreads / 32][15 * 128];
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t *mask = s_mask[threadIdx.x >> 5];
+    const uint4 *cur = nullptr;  // schedule whose masks are in `mask`
+    for (;;) {
+        const unsigned long long t = claim_tile(counter, total_tiles, order);
+        if (t >= total_tiles)
+            break;
+        const BatchReq rq = reqs[__ldg(tile_req + t)];
+        uint64_t first, last;
+        aestile::tile_blocks_of(t - rq.tile_begin, tile_groups, rq.iv_lo & 255u, (rq.len + 15) >> 4, &first,
+                                &last);
+        if (rq.rk != cur) {
+            __syncwarp();  // every lane is done with the previous masks
+            aesbs::build_masks(mask, reinterpret_cast<const uint32_t *>(rq.rk), (int)rq.nr, lane, 32);
+            __syncwarp();
+            cur = rq.rk;
+        }
+        const uint4 k0 = __ldg(rq.rk);
+        const uint32_t rk0[4] = {k0.x, k0.y, k0.z, k0.w};
+        const aesbs::MaskKeys keys{reinterpret_cast<const uint4 *>(mask)};
+        switch (rq.nr) {
+        case 10: aesbs::xor_range<10>(rq.in, rq.out, rq.len, rq.iv_hi, rq.iv_lo, rk0, first, last, 0, 1, keys); break;
+        case 12: aesbs::xor_range<12>(rq.in, rq.out, rq.len, rq.iv_hi, rq.iv_lo, rk0, first, last, 0, 1, keys); break;
+        default: aesbs::xor_range<14>(rq.in, rq.out, rq.len, rq.iv_hi, rq.iv_lo, rk0, first, last, 0, 1, keys); break;
+        }
+    }
+}
+
+template <int NB, int MAXT, bool RK_REGS, bool SEARCH>
+cudaError_t set_smem_attr()
+{
+    const size_t bytes = aestt::kTableBytes + (SEARCH ? sizeof(uint64_t) * aesrt::kSearchMaxReqs : 0);
+    return cudaFuncSetAttribute(batch_ttable_kernel<NB, MAXT, RK_REGS, SEARCH>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <bool SEARCH>
+cudaError_t set_smem_attrs()
+{
+    cudaError_t e;
+    if ((e = set_smem_attr<1, kRegsMaxThreads, true, SEARCH>()) ||
+        (e = set_smem_attr<2, kRegsMaxThreads, true, SEARCH>()) ||
+        (e = set_smem_attr<4, kRegsMaxThreads, true, SEARCH>()) || (e = set_smem_attr<1, 1024, false, SEARCH>()) ||
+        (e = set_smem_attr<2, 1024, false, SEARCH>()) || (e = set_smem_attr<4, 1024, false, SEARCH>()))
+        return e;
+    return cudaSuccess;
+}
+
+// Launch the T-table kernel for shape s (nb and the CTA size pick the
+// instantiation).
+template <bool SEARCH>
+cudaError_t launch_ttable(int ctas, const aesrt::BatchShape &s, size_t smem, cudaStream_t stream,
+                          const BatchReq *reqs, const uint32_t *map, int nreq, uint64_t total,
+                          unsigned long long *counter, const uint32_t *te0, uint32_t tg, TileOrder order)
+{
+#define AES_BATCH_LAUNCH(NB, MAXT, REGS)                                                                   \
+    batch_ttable_kernel<NB, MAXT, REGS, SEARCH><<<ctas, s.threads, smem, stream>>>(reqs, map, nreq, total, \
+                                                                                   counter, te0, tg, order)
+    const bool regs = s.threads <= kRegsMaxThreads;
+    switch (s.nb) {
+    case 1:
+        if (regs)
+            AES_BATCH_LAUNCH(1, kRegsMaxThreads, true);
+        else
+            AES_BATCH_LAUNCH(1, 1024, false);
+        break;
+    case 4:
+        if (regs)
+            AES_BATCH_LAUNCH(4, kRegsMaxThreads, true);
+        else
+            AES_BATCH_LAUNCH(4, 1024, false);
+        break;
+    default:
+        if (regs)
+            AES_BATCH_LAUNCH(2, kRegsMaxThreads, true);
+        else
+            AES_BATCH_LAUNCH(2, 1024, false);
+        break;
+    }
+#undef AES_BATCH_LAUNCH
+    return cudaGetLastError();
+}
+
+int g_bs_ctas_per_sm = 1;  // resident bitsliced batch CTAs per SM (set with the attributes)
+
 }  // namespace
 
 namespace aesrt {
 
-constexpr size_t kBatchSmem = aestt::kTableBytes;
-
 cudaError_t batch_set_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_ttable_kernel<2, kRegsMaxThreads, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
-    if (!e)
-        e = cudaFuncSetAttribute(batch_ttable_kernel<2, 1024, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kBatchSmem);
-    return e;
+    cudaError_t e;
+    if ((e = set_smem_attrs<false>()) || (e = set_smem_attrs<true>()))
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_bitslice_kernel, kBsThreads, 0)))
+        return e;
+    g_bs_ctas_per_sm = per_sm > 0 ? per_sm : 1;
+    return cudaSuccess;
 }
 
+cudaError_t launch_batch_search(const BatchReq *reqs, int n, uint64_t total_tiles, unsigned long long *counter,
+                                const uint32_t *te0, const BatchShape &s, int nsm, cudaStream_t stream)
+{
+    if (n < 1 || n > kSearchMaxReqs || s.variant != AES_VARIANT_TTABLE)
+        return cudaErrorInvalidValue;
+    int ctas = s.ctas > 0 ? std::min(s.ctas, nsm) : nsm;
+    if ((uint64_t)ctas > total_tiles)
+        ctas = (int)total_tiles;
+    const size_t smem = aestt::kTableBytes + sizeof(uint64_t) * (size_t)n;
+    return launch_ttable<true>(ctas, s, smem, stream, reqs, nullptr, n, total_tiles, counter, te0,
+                               (uint32_t)(s.tile_blocks / 256), TileOrder{1, 0});
+}
 
 static uint64_t gcd64(uint64_t a, uint64_t b)
 {
@@ -143,8 +295,18 @@ struct BatchTables {
     int64_t bytes = 0;
 };
 
-static int validate_batch_shape(BatchShape &s)
+int validate_batch_shape(BatchShape &s)
 {
+    if (s.variant == AES_VARIANT_AUTO)
+        s.variant = AES_VARIANT_TTABLE;
+    if (s.variant == AES_VARIANT_BITSLICE) {
+        if (s.threads != kBsThreads)
+            return AES_EINVAL;  // one instantiation: 128-thread CTAs
+    } else if (s.variant != AES_VARIANT_TTABLE) {
+        return AES_EINVAL;
+    }
+    if (s.nb != 1 && s.nb != 2 && s.nb != 4)
+        return AES_EINVAL;
     if (s.threads < 32 || s.threads > 1024 || (s.threads & 31))
         return AES_EINVAL;
     if (s.tile_blocks < 256 || s.tile_blocks % 256 || s.tile_blocks > (1 << 22))
@@ -158,27 +320,21 @@ static BatchShape pick_batch_shape(const DeviceState &st, const aes_batch_opts_t
 {
     BatchShape s = st.batch_tuned;
     if (opts) {
+        if (opts->variant && opts->variant != s.variant) {
+            // another variant than the tuned one: start from its defaults
+            s = opts->variant == AES_VARIANT_BITSLICE ? BatchShape{AES_VARIANT_BITSLICE, kBsThreads, 2048, 0, 1}
+                                                      : BatchShape{opts->variant, 512, 2048, 0, 2};
+        }
         if (opts->threads)
             s.threads = opts->threads;
         if (opts->tile_blocks)
             s.tile_blocks = opts->tile_blocks;
         if (opts->ctas)
             s.ctas = opts->ctas;
-        if (opts->variant)
-            s.variant = opts->variant;
+        if (opts->blocks_per_thread)
+            s.nb = opts->blocks_per_thread;
     }
     return s;
-}
-
-// Tiles of a request: whole counter groups, tile_blocks / 256 per tile.
-static uint64_t tiles_of(uint64_t len, uint32_t iv_low_byte, int tile_blocks)
-{
-    const uint64_t nb = (len + 15) / 16;
-    if (!nb)
-        return 0;
-    const uint64_t groups = ((iv_low_byte + nb - 1) >> 8) + 1;
-    const uint64_t per = (uint64_t)tile_blocks / 256u;
-    return (groups + per - 1) / per;
 }
 
 static int build_tables(const aes_desc_t *descs, int n, int dev, const BatchShape &s, BatchTables &bt)
@@ -245,7 +401,10 @@ cudaError_t launch_batch_image(uint8_t *img, const DeviceImage &im, const BatchT
     cudaError_t e = cudaMemsetAsync(img + im.off_counter, 0, sizeof(unsigned long long), stream);
     if (e)
         return e;
-    int ctas = s.ctas > 0 ? std::min(s.ctas, nsm) : nsm;
+    // persistent CTAs: as many as are resident at once (one T-table CTA
+    // per SM: its tables take 128 KiB of shared memory)
+    const int resident = s.variant == AES_VARIANT_BITSLICE ? nsm * g_bs_ctas_per_sm : nsm;
+    int ctas = s.ctas > 0 ? std::min(s.ctas, resident) : resident;
     if ((uint64_t)ctas > bt.total_tiles)
         ctas = (int)bt.total_tiles;
     const TileOrder order = make_order(bt.total_tiles, seed);
@@ -253,13 +412,12 @@ cudaError_t launch_batch_image(uint8_t *img, const DeviceImage &im, const BatchT
     const uint32_t *map = reinterpret_cast<const uint32_t *>(img + im.off_map);
     unsigned long long *counter = reinterpret_cast<unsigned long long *>(img + im.off_counter);
     const uint32_t tg = (uint32_t)(s.tile_blocks / 256);
-    if (s.threads <= kRegsMaxThreads)
-        batch_ttable_kernel<2, kRegsMaxThreads, true>
-            <<<ctas, s.threads, kBatchSmem, stream>>>(reqs, map, bt.total_tiles, counter, te0, tg, order);
-    else
-        batch_ttable_kernel<2, 1024, false>
-            <<<ctas, s.threads, kBatchSmem, stream>>>(reqs, map, bt.total_tiles, counter, te0, tg, order);
-    return cudaGetLastError();
+    if (s.variant == AES_VARIANT_BITSLICE) {
+        batch_bitslice_kernel<<<ctas, kBsThreads, 0, stream>>>(reqs, map, bt.total_tiles, counter, tg, order);
+        return cudaGetLastError();
+    }
+    return launch_ttable<false>(ctas, s, aestt::kTableBytes, stream, reqs, map, (int)bt.reqs.size(),
+                                bt.total_tiles, counter, te0, tg, order);
 }
 
 }  // namespace aesrt

@@ -15,18 +15,22 @@
 //
 // In host code the array's name is only a host-side stand-in, not a device
 // address, so the first call on each device looks up the real address with
-// cudaGetSymbolAddress (with that device current) and caches it; that first
-// call should therefore come before any stream capture.  All calls share the
-// one array and it keeps the previous call's contents: the claim counter is
-// cleared on every call, and calls whose work overlaps on the GPU (two
-// streams, or two threads) race on the array -- callers must serialise them.
+// cudaGetSymbolAddress (with that device current) and caches it.  All calls
+// share the one array and it keeps the previous call's contents: the claim
+// counter is cleared on every call, and calls whose work overlaps on the GPU
+// (two streams, or two threads) race on the array -- callers must serialise
+// them.  A call copies its descriptors from a stack buffer with
+// cudaMemcpyAsync (pageable host memory), so it must not be made while its
+// stream is being captured into a CUDA graph; callers that want a graph use
+// the batch plans (aes_batch_plan_create), which allocate once up front.
+//
+// The kernel is the batch kernel's search variant (batch.cu): the same
+// persistent T-table CTAs, tiles of whole counter groups claimed by each warp
+// from one counter, and the owner of a claimed tile found by a binary search
+// over the requests' first tiles in shared memory instead of a tile map.
 #include "../../include/aesoffload.h"
 #include "internal.h"
 #include "runtime.h"
-#include "common.cuh"
-#include "aes_ttable.cuh"
-#include "tile.cuh"
-
 #include <cstring>
 #include <mutex>
 
@@ -35,9 +39,9 @@ namespace {
 using aesrt::BatchReq;
 
 constexpr int kMaxReqs = AES_NOALLOC_MAX_REQUESTS;
+static_assert(kMaxReqs <= aesrt::kSearchMaxReqs, "the search kernel holds every request's first tile");
 constexpr size_t kReqBytes = sizeof(BatchReq) * (size_t)kMaxReqs;  // 64 KiB
 constexpr size_t kScratchBytes = kReqBytes + 256;                    // + claim counter
-constexpr size_t kSmem = aestt::kTableBytes + sizeof(uint64_t) * (size_t)kMaxReqs;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
@@ -47,61 +51,6 @@ struct ScratchAddress {
     cudaError_t err = cudaSuccess;
 };
 static ScratchAddress g_scratch[aesrt::kMaxDevices];
-
-// The batch kernel without a tile map: each CTA copies the requests' first
-// tile numbers into shared memory and finds the owner of a claimed tile by
-// binary search.
-template <int NB>
-__global__ void __launch_bounds__(1024, 1)
-    batch_noalloc_kernel(const BatchReq *__restrict__ reqs, int n, uint64_t total_tiles,
-                         unsigned long long *__restrict__ counter, const uint32_t *__restrict__ te0,
-                         uint32_t tile_blocks)
-{
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *s_begin = reinterpret_cast<uint64_t *>(smem + aestt::kTableBytes);
-    __shared__ uint4 s_rk[15];
-    __shared__ unsigned long long s_tile;
-    __shared__ int s_req;
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        s_begin[i] = reqs[i].tile_begin;
-    aestt::fill_tables(smem, te0);
-    const aestt::Lanes ln;
-    __syncthreads();
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned long long t = atomicAdd(counter, 1ull);
-            if (t < total_tiles) {
-                int lo = 0, hi = n - 1;  // last request whose first tile is <= t
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_begin[mid] <= t)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
-                }
-                s_req = lo;
-            }
-            s_tile = t;
-        }
-        __syncthreads();
-        const unsigned long long t = s_tile;
-        if (t >= total_tiles)
-            break;
-        const BatchReq rq = reqs[s_req];
-        if (threadIdx.x <= rq.nr)
-            s_rk[threadIdx.x] = rq.rk[threadIdx.x];
-        __syncthreads();
-        const uint64_t nblocks = (rq.len + 15) >> 4;
-        const uint64_t first = (t - rq.tile_begin) * tile_blocks;
-        const uint64_t last = min(first + tile_blocks, nblocks);
-        switch (rq.nr) {
-        case 10: aestile::run_tile<10, NB>(rq, first, last, smem, ln, s_rk); break;
-        case 12: aestile::run_tile<12, NB>(rq, first, last, smem, ln, s_rk); break;
-        default: aestile::run_tile<14, NB>(rq, first, last, smem, ln, s_rk); break;
-        }
-        __syncthreads();
-    }
-}
 
 }  // namespace
 
@@ -122,17 +71,13 @@ extern "C" int aes_ctr_batch_noalloc(const aes_desc_t *descs, int n, void *strea
     ScratchAddress &sa = g_scratch[st->device];
     std::call_once(sa.once, [&sa] {
         sa.err = cudaGetSymbolAddress(reinterpret_cast<void **>(&sa.ptr), g_noalloc_scratch);
-        if (sa.err == cudaSuccess) {
-            sa.err = cudaFuncSetAttribute(batch_noalloc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kSmem);
-            if (sa.err == cudaSuccess)
-                sa.err = cudaFuncSetAttribute(batch_noalloc_kernel<2>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        }
     });
     if (sa.err != cudaSuccess)
         return cuda_fail(sa.err, "aes_ctr_batch_noalloc set-up");
-    const BatchShape s = st->batch_tuned;
+    // the tuned T-table shape (the search kernel has no bitsliced variant)
+    BatchShape s = st->batch_tuned;
+    if (s.variant != AES_VARIANT_TTABLE)
+        s = BatchShape{AES_VARIANT_TTABLE, 512, 2048, 0, 2};
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     // Validate every request before touching the shared scratch.
     uint64_t tiles = 0;
@@ -145,7 +90,7 @@ extern "C" int aes_ctr_batch_noalloc(const aes_desc_t *descs, int n, void *strea
             void *dout = nullptr;
             if ((rc = check_payload(d.in, d.out, d.len, st->device, &din, &dout)))
                 return rc;
-            tiles += ((d.len + 15) / 16 + (uint64_t)s.tile_blocks - 1) / (uint64_t)s.tile_blocks;
+            tiles += tiles_of(d.len, d.iv[15], s.tile_blocks);
         }
     }
     if (tiles == 0)
@@ -173,7 +118,7 @@ extern "C" int aes_ctr_batch_noalloc(const aes_desc_t *descs, int n, void *strea
                 check_payload(d.in, d.out, d.len, st->device, &din, &dout);
                 r.in = static_cast<const uint4 *>(din);
                 r.out = static_cast<uint4 *>(dout);
-                begin += ((d.len + 15) / 16 + (uint64_t)s.tile_blocks - 1) / (uint64_t)s.tile_blocks;
+                begin += tiles_of(d.len, d.iv[15], s.tile_blocks);
             }
         }
         e = cudaMemcpyAsync(sa.ptr + sizeof(BatchReq) * (size_t)i0, chunk, sizeof(BatchReq) * (size_t)cnt,
@@ -184,16 +129,7 @@ extern "C" int aes_ctr_batch_noalloc(const aes_desc_t *descs, int n, void *strea
         e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), cs);
     if (e)
         return cuda_fail(e, "aes_ctr_batch_noalloc copy");
-    int ctas = s.ctas > 0 ? (s.ctas < st->nsm ? s.ctas : st->nsm) : st->nsm;
-    if ((uint64_t)ctas > tiles)
-        ctas = (int)tiles;
-    const BatchReq *reqs = reinterpret_cast<const BatchReq *>(sa.ptr);
-    if (s.tile_blocks / s.threads >= 2)
-        batch_noalloc_kernel<2><<<ctas, s.threads, kSmem, cs>>>(reqs, n, tiles, counter, st->te0,
-                                                                  (uint32_t)s.tile_blocks);
-    else
-        batch_noalloc_kernel<1><<<ctas, s.threads, kSmem, cs>>>(reqs, n, tiles, counter, st->te0,
-                                                                  (uint32_t)s.tile_blocks);
-    e = cudaGetLastError();
-    return e ? cuda_fail(e, "batch_noalloc_kernel") : AES_OK;
+    e = launch_batch_search(reinterpret_cast<const BatchReq *>(sa.ptr), n, tiles, counter, st->te0, s, st->nsm,
+                            cs);
+    return e ? cuda_fail(e, "aes_ctr_batch_noalloc launch") : AES_OK;
 }

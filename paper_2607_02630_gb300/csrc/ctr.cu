@@ -16,7 +16,7 @@
 #include "internal.h"
 #include "common.cuh"
 #include "aes_ttable.cuh"
-#include "aes_bitslice.cuh"
+#include "bs_tile.cuh"
 #include "tile.cuh"
 
 namespace {
@@ -38,86 +38,17 @@ __global__ void __launch_bounds__(1024, 1) ctr_ttable_kernel(const __grid_consta
                                ln, rk);
 }
 
-// Bit-plane masks of the round keys: mask[r*128 + P] = all-ones iff bit P of
-// round key r is set (P = 8*byte + bit).
-struct BsKeys {
-    const uint4 *m;
-    __device__ __forceinline__ uint32_t operator()(int r, int P) const
-    {
-        const uint4 q = m[r * 32 + (P >> 2)];
-        return (P & 3) == 0 ? q.x : (P & 3) == 1 ? q.y : (P & 3) == 2 ? q.z : q.w;
-    }
-};
-
 template <int NR>
 __global__ void __launch_bounds__(128) ctr_bitslice_kernel(const __grid_constant__ CtrParams p)
 {
     __shared__ __align__(16) uint32_t bsk[(NR + 1) * 128];
-    for (int q = threadIdx.x; q < (NR + 1) * 128; q += blockDim.x) {
-        const int r = q >> 7, P = q & 127;
-        const uint32_t word = p.rk[4 * r + (P >> 5)];
-        bsk[q] = ((word >> (P & 31)) & 1u) ? 0xffffffffu : 0u;
-    }
+    aesbs::build_masks(bsk, p.rk, NR, threadIdx.x, blockDim.x);
     __syncthreads();
-    const BsKeys keys{reinterpret_cast<const uint4 *>(bsk)};
-    const uint64_t nfull = p.len >> 4;
-    const uint32_t tail = (uint32_t)(p.len & 15);
-    const uint64_t nblocks = nfull + (tail ? 1 : 0);
-    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t rk0[4] = {p.rk[0], p.rk[1], p.rk[2], p.rk[3]};
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t base = gwarp * 1024; base < nblocks; base += nwarps * 1024) {
-        uint32_t x[128];
-        const uint64_t j0 = base + lane;  // block k of this lane is j0 + 32k
-        uint32_t c0[4];
-        aesdev::counter_block(p.iv_hi, p.iv_lo, j0, c0);
-        const uint32_t L = aesdev::bswap32(c0[3]);
-        if (L <= 0xffffffffu - 31u * 32u) {
-            // The 32 counters differ only in their last word: the planes of
-            // bytes 0..11 are all-zeros/all-ones masks (round key 0 folded in).
-#pragma unroll
-            for (int w = 0; w < 3; ++w) {
-                const uint32_t v = c0[w] ^ p.rk[w];
-#pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    x[32 * w + q] = 0u - ((v >> q) & 1u);
-            }
-#pragma unroll
-            for (int k = 0; k < 32; ++k)
-                x[96 + k] = aesdev::bswap32(L + 32u * (uint32_t)k) ^ p.rk[3];
-            aesbs::transpose32(x + 96);
-        } else {
-            // A carry leaves the low word inside this lane's 32 blocks.
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                uint32_t c[4];
-                aesdev::counter_block(p.iv_hi, p.iv_lo, j0 + 32u * (uint32_t)k, c);
-#pragma unroll
-                for (int w = 0; w < 4; ++w)
-                    x[32 * w + k] = c[w] ^ p.rk[w];
-            }
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-                aesbs::transpose32(x + 32 * w);
-        }
-        aesbs::encrypt_rounds<NR>(x, keys);
-#pragma unroll
-        for (int w = 0; w < 4; ++w)
-            aesbs::transpose32(x + 32 * w);
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const uint64_t j = j0 + 32u * (uint32_t)k;
-            if (j < nfull) {
-                const uint4 pt = aesdev::ld_stream(p.in + j);
-                aesdev::st_stream(p.out + j, make_uint4(pt.x ^ x[k], pt.y ^ x[32 + k],
-                                                        pt.z ^ x[64 + k], pt.w ^ x[96 + k]));
-            } else if (j == nfull && tail) {
-                aesdev::xor_tail(reinterpret_cast<const uint8_t *>(p.in + j),
-                                 reinterpret_cast<uint8_t *>(p.out + j), x[k], x[32 + k], x[64 + k],
-                                 x[96 + k], tail);
-            }
-        }
-    }
+    aesbs::xor_range<NR>(p.in, p.out, p.len, p.iv_hi, p.iv_lo, rk0, 0, (p.len + 15) >> 4, gwarp, nwarps,
+                         aesbs::MaskKeys{reinterpret_cast<const uint4 *>(bsk)});
 }
 
 template <int NR>

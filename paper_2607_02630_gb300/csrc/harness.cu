@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <deque>
 #include <thread>
 #include <vector>
 
@@ -175,7 +176,13 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess)
                 free_ev.push_back(e);
         }
-        std::vector<std::pair<cudaEvent_t, int>> pending;
+        // Events recorded on one stream complete in the order they were
+        // recorded, so only the oldest pending one is queried: a thread
+        // makes at most one cudaEventQuery per loop pass however many of
+        // its requests are in flight (querying every pending event made
+        // eight threads contend on the driver and capped the baseline far
+        // below what the same launches sustain from one stream).
+        std::deque<std::pair<cudaEvent_t, int>> pending;
         int next = k;
         double last_progress = seconds_since(t0);
         while (next < n || !pending.empty()) {
@@ -203,13 +210,11 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
                 }
                 next += nthreads;
             }
-            for (size_t i = 0; i < pending.size();) {
-                const cudaError_t q = cudaEventQuery(pending[i].first);
-                if (q == cudaErrorNotReady) {
-                    ++i;
-                    continue;
-                }
-                const int idx = pending[i].second;
+            while (!pending.empty()) {
+                const cudaError_t q = cudaEventQuery(pending.front().first);
+                if (q == cudaErrorNotReady)
+                    break;
+                const int idx = pending.front().second;
                 const double now = seconds_since(t0);
                 last_progress = now;
                 if (q == cudaSuccess) {
@@ -220,9 +225,8 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
                     latency_us[idx] = -1.0;
                     sh.errors.fetch_add(1);
                 }
-                free_ev.push_back(pending[i].first);
-                pending[i] = pending.back();
-                pending.pop_back();
+                free_ev.push_back(pending.front().first);
+                pending.pop_front();
             }
         }
         cudaStreamSynchronize(s);

@@ -54,12 +54,33 @@ struct BatchReq {        // one request, device-side descriptor (64 bytes)
 static_assert(sizeof(BatchReq) == 64, "descriptor is one 64-byte line");
 
 struct BatchShape {
-    int variant;
+    int variant;      // AES_VARIANT_TTABLE or AES_VARIANT_BITSLICE
     int threads;
-    int tile_blocks;
+    int tile_blocks;  // a multiple of 256: tiles are runs of whole counter groups
     int ctas;
+    int nb;           // T-table: blocks each lane keeps in flight (1, 2 or 4)
 };
 
+// Tiles of one batch request of `len` bytes whose initial counter has low
+// byte `iv_low_byte`: runs of tile_blocks / 256 whole 256-block counter
+// groups (group g holds the blocks whose counter low byte wrapped g times).
+inline uint64_t tiles_of(uint64_t len, uint32_t iv_low_byte, int tile_blocks)
+{
+    const uint64_t nb = (len + 15) / 16;
+    if (!nb)
+        return 0;
+    const uint64_t groups = ((iv_low_byte + nb - 1) >> 8) + 1;
+    const uint64_t per = (uint64_t)tile_blocks / 256u;
+    return (groups + per - 1) / per;
+}
+
 cudaError_t batch_set_attributes();
+// The persistent T-table batch kernel over requests reqs[0..n) whose tiles
+// start at reqs[i].tile_begin; the owner of a claimed tile is found by a
+// binary search over those starts in shared memory (no tile map, so the
+// caller needs no scratch beyond reqs and the claim counter).  n <= 1024.
+cudaError_t launch_batch_search(const BatchReq *reqs, int n, uint64_t total_tiles, unsigned long long *counter,
+                                const uint32_t *te0, const BatchShape &s, int nsm, cudaStream_t stream);
+constexpr int kSearchMaxReqs = 1024;
 
 }  // namespace aesrt

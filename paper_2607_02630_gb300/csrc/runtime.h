@@ -44,6 +44,8 @@ void iv_halves(const uint8_t *iv, uint64_t *hi, uint64_t *lo);
 // tune.cu
 void tune_defaults(DeviceState &st);
 int validate_ctr_shape(const CtrShape &s);
+// batch.cu: AES_OK for a shape the batch kernels take (AUTO becomes T-table)
+int validate_batch_shape(BatchShape &s);
 CtrShape tuned_ctr_shape(const DeviceState &st, size_t len, int nr);
 int len_bucket(size_t len);
 

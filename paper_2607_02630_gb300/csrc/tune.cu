@@ -58,7 +58,7 @@ void tune_defaults(DeviceState &st)
     for (int i = 0; i < 3; ++i)
         for (int b = 0; b < kLenBuckets; ++b)
             st.ctr_tuned[i][b] = default_shape(st.nsm, b);
-    st.batch_tuned = BatchShape{AES_VARIANT_TTABLE, 512, 2048, 0};
+    st.batch_tuned = BatchShape{AES_VARIANT_TTABLE, 512, 2048, 0, 2};
 }
 
 CtrShape tuned_ctr_shape(const DeviceState &st, size_t len, int nr)
@@ -93,10 +93,71 @@ float time_ctr(aes_ctx_t ctx, const uint8_t *iv, void *buf_in, void *buf_out, si
     return t[t.size() / 2];
 }
 
-// Batch shape: time the persistent batch kernel (graph plans, CUDA events)
-// on a synthetic mixed batch in [in, in + cap) -> [out, ...): lengths spread
-// log-uniformly over 1 KiB .. 8 MiB by a fixed LCG, AES-128 and AES-256
-// alternating, 256-byte aligned offsets; keep the fastest (threads, tile).
+// The batch kernel's candidate shapes: T-table CTAs of 256, 512 (round keys
+// in registers) and 1024 threads (keys in shared memory) x 1, 2 or 4 blocks
+// per lane in flight x tiles of 4, 8 or 16 counter groups; and the bitsliced
+// kernel (128-thread CTAs) x the same tiles.
+std::vector<BatchShape> batch_candidates()
+{
+    std::vector<BatchShape> c;
+    for (int tb : {1024, 2048, 4096}) {
+        for (int th : {256, 512, 1024})
+            for (int nb : {1, 2, 4})
+                c.push_back(BatchShape{AES_VARIANT_TTABLE, th, tb, 0, nb});
+        c.push_back(BatchShape{AES_VARIANT_BITSLICE, 128, tb, 0, 1});
+    }
+    return c;
+}
+
+// Time every candidate as a graph plan over `reqs` (median of `reps` launches
+// after two warm-ups, CUDA events on `s`); the fastest in *pick.  Returns
+// AES_OK, or the first error if no candidate ran.
+int sweep_batch(const std::vector<aes_desc_t> &reqs, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps,
+                BatchShape *pick, float *best_ms)
+{
+    float best = 1e30f;
+    int err = AES_EINVAL;
+    for (const BatchShape &c : batch_candidates()) {
+        aes_batch_opts_t o{};
+        o.variant = c.variant;
+        o.threads = c.threads;
+        o.tile_blocks = c.tile_blocks;
+        o.blocks_per_thread = c.nb;
+        aes_batch_plan_t plan = nullptr;
+        if ((err = aes_batch_plan_create(&plan, reqs.data(), (int)reqs.size(), &o)) != AES_OK)
+            continue;
+        std::vector<float> t;
+        for (int r = 0; r < reps + 2; ++r) {
+            cudaEventRecord(a, s);
+            const int lr = aes_batch_plan_launch(plan, s);
+            cudaEventRecord(b, s);
+            if (lr != AES_OK || cudaEventSynchronize(b) != cudaSuccess) {
+                err = lr != AES_OK ? lr : AES_ECUDA;
+                t.clear();
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            if (r >= 2)
+                t.push_back(ms);
+        }
+        aes_batch_plan_destroy(plan);
+        if (t.empty())
+            continue;
+        std::sort(t.begin(), t.end());
+        if (t[t.size() / 2] < best) {
+            best = t[t.size() / 2];
+            *pick = c;
+        }
+    }
+    if (best_ms)
+        *best_ms = best;
+    return best < 1e30f ? AES_OK : err;
+}
+
+// Batch shape on a synthetic mixed batch in [in, in + cap) -> [out, ...):
+// lengths spread log-uniformly over 1 KiB .. 8 MiB by a fixed LCG, AES-128
+// and AES-256 alternating, 256-byte aligned offsets.
 int tune_batch(DeviceState &st, void *in, void *out, size_t cap, cudaStream_t s, cudaEvent_t a, cudaEvent_t b)
 {
     const uint8_t key[32] = {7, 1, 3};
@@ -122,44 +183,9 @@ int tune_batch(DeviceState &st, void *in, void *out, size_t cap, cudaStream_t s,
         reqs.push_back(d);
         off += (len + 255) / 256 * 256;
     }
-    const int threads[] = {256, 384, 512, 1024};
-    const int tiles[] = {1024, 2048, 4096};
-    float best = 1e30f;
     BatchShape pick = st.batch_tuned;
-    for (int th : threads) {
-        for (int tb : tiles) {
-            if (rc)
-                break;
-            aes_batch_opts_t o{};
-            o.threads = th;
-            o.tile_blocks = tb;
-            aes_batch_plan_t plan = nullptr;
-            if (aes_batch_plan_create(&plan, reqs.data(), (int)reqs.size(), &o) != AES_OK)
-                continue;
-            std::vector<float> t;
-            for (int r = 0; r < 8; ++r) {
-                cudaEventRecord(a, s);
-                const int lr = aes_batch_plan_launch(plan, s);
-                cudaEventRecord(b, s);
-                if (lr != AES_OK || cudaEventSynchronize(b) != cudaSuccess) {
-                    t.clear();
-                    break;
-                }
-                float ms = 0;
-                cudaEventElapsedTime(&ms, a, b);
-                if (r >= 2)
-                    t.push_back(ms);
-            }
-            aes_batch_plan_destroy(plan);
-            if (t.empty())
-                continue;
-            std::sort(t.begin(), t.end());
-            if (t[t.size() / 2] < best) {
-                best = t[t.size() / 2];
-                pick = BatchShape{AES_VARIANT_TTABLE, th, tb, 0};
-            }
-        }
-    }
+    if (!rc)
+        rc = sweep_batch(reqs, s, a, b, 6, &pick, nullptr);
     aes_ctx_destroy(ctx[0]);
     aes_ctx_destroy(ctx[1]);
     if (!rc)
@@ -263,10 +289,66 @@ int aes_autotune(const char *path)
                 std::fprintf(f, "  [%d, %d, %d, %d, %d]%s\n", ki, bk, c.variant, c.threads, c.nb,
                              (ki == 2 && bk == kLenBuckets - 1) ? "" : ",");
             }
-        std::fprintf(f, "],\n\"batch\": [%d, %d, %d]}\n", st->batch_tuned.variant,
-                     st->batch_tuned.threads, st->batch_tuned.tile_blocks);
+        std::fprintf(f, "],\n\"batch\": [%d, %d, %d, %d]}\n", st->batch_tuned.variant,
+                     st->batch_tuned.threads, st->batch_tuned.tile_blocks, st->batch_tuned.nb);
         std::fclose(f);
     }
+    return AES_OK;
+}
+
+int aes_batch_autotune(const aes_desc_t *descs, int n, void *stream, aes_batch_opts_t *best)
+{
+    if (n < 1 || !descs)
+        return AES_EINVAL;
+    if (n > AES_BATCH_MAX)
+        return AES_ETOOBIG;
+    DeviceState *st = nullptr;
+    int rc = device_state(&st);
+    if (rc)
+        return rc;
+    const std::vector<aes_desc_t> reqs(descs, descs + n);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (!e)
+        e = cudaEventCreate(&b);
+    if (e) {
+        if (a)
+            cudaEventDestroy(a);
+        return cuda_fail(e, "aes_batch_autotune events");
+    }
+    BatchShape pick = st->batch_tuned;
+    rc = sweep_batch(reqs, s, a, b, 5, &pick, nullptr);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc)
+        return rc;
+    st->batch_tuned = pick;
+    if (best) {
+        std::memset(best, 0, sizeof(*best));
+        best->variant = pick.variant;
+        best->threads = pick.threads;
+        best->tile_blocks = pick.tile_blocks;
+        best->ctas = pick.ctas;
+        best->blocks_per_thread = pick.nb;
+    }
+    return AES_OK;
+}
+
+int aes_batch_tuned_shape(aes_batch_opts_t *out)
+{
+    if (!out)
+        return AES_EINVAL;
+    DeviceState *st = nullptr;
+    int rc = device_state(&st);
+    if (rc)
+        return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->variant = st->batch_tuned.variant;
+    out->threads = st->batch_tuned.threads;
+    out->tile_blocks = st->batch_tuned.tile_blocks;
+    out->ctas = st->batch_tuned.ctas;
+    out->blocks_per_thread = st->batch_tuned.nb;
     return AES_OK;
 }
 
@@ -302,8 +384,13 @@ int aes_autotune_load(const char *path)
             }
             continue;
         }
-        if (std::sscanf(line, "\"batch\": [%d, %d, %d]", &v, &t, &nb) == 3)
-            bs = BatchShape{v, t, nb, 0};
+        int tb = 0, bnb = 2;
+        const int got = std::sscanf(line, "\"batch\": [%d, %d, %d, %d]", &v, &t, &tb, &bnb);
+        if (got == 3 || got == 4) {  // three fields: written before blocks per lane were tuned (2)
+            BatchShape c{v, t, tb, 0, got == 4 ? bnb : 2};
+            if (validate_batch_shape(c) == AES_OK)
+                bs = c;
+        }
     }
     std::fclose(f);
     if (sms != st->nsm || std::strcmp(name, st->name) != 0)

@@ -1,4 +1,6 @@
 """Helpers shared by the GPU parity tests (device buffers, oracle calls)."""
+import json
+
 import numpy as np
 
 
@@ -34,3 +36,18 @@ def iv_with_low(g, kind: str) -> np.ndarray:
     else:
         raise ValueError(kind)
     return np.frombuffer(v.to_bytes(16, "big"), np.uint8).copy()
+
+
+def set_batch_shape(torch, aes, path, shape):
+    """Make `shape` = (variant, threads, tile_blocks, blocks_per_thread) the
+    device's tuned batch shape by loading a table file (aes_autotune_load)
+    written for this device; returns the shape that was in place before."""
+    before = aes.batch_tuned_shape()
+    props = torch.cuda.get_device_properties(0)
+    head = json.dumps({"device": props.name, "sms": props.multi_processor_count}).rstrip("}")
+    # one ctr row (bucket 0, the default shape) -- the loader wants at least one
+    path.write_text(head + ', "ctr": [\n  [0, 0, 1, 256, 1]\n],\n"batch": [%d, %d, %d, %d]}\n' % tuple(shape))
+    aes.autotune_load(str(path))
+    got = aes.batch_tuned_shape()
+    assert (got["variant"], got["threads"], got["tile_blocks"], got["blocks_per_thread"]) == tuple(shape), got
+    return (before["variant"], before["threads"], before["tile_blocks"], before["blocks_per_thread"])

@@ -95,6 +95,10 @@ def test_host_side_argument_errors(lib):
     assert lib.offload_server_destroy(None) == A.AES_OK
     assert lib.aes_autotune_load(None) == A.AES_EINVAL
     assert lib.aes_tuned_shape(4096, 100, None) == A.AES_EINVAL
+    assert lib.aes_batch_autotune(None, 0, None, None) == A.AES_EINVAL
+    assert lib.aes_batch_autotune(None, 3, None, None) == A.AES_EINVAL
+    assert lib.aes_batch_tuned_shape(None) == A.AES_EINVAL
+    assert lib.aes_measure_peaks(None) == A.AES_EINVAL
 
 
 def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
@@ -110,6 +114,7 @@ MIRRORS = {
     "aes_launch_t": A.LaunchShape,
     "aes_desc_t": A.Desc,
     "aes_batch_opts_t": A.BatchOpts,
+    "aes_peaks_t": A.Peaks,
     "offload_cfg_t": A.ServerCfg,
     "offload_stats_t": A.ServerStats,
     "aes_drive_result_t": A.DriveResult,

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from paper_2607_02630_gb300 import workloads as W
 
-from gpu_util import iv_plus, iv_with_low, to_dev, to_host
+from gpu_util import iv_plus, iv_with_low, set_batch_shape, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -45,16 +45,51 @@ def mixed_lengths(g, k):
     return fixed + rand
 
 
-@pytest.mark.parametrize("tile_blocks,threads", [(1024, 1024), (2048, 512), (8192, 1024), (512, 256), (4096, 512),
-                                                 (1024, 544), (2048, 0)])
-def test_mixed_batch_matches_oracle(cuda, aes, ncpu, tile_blocks, threads):
-    g = W.rng(40 + tile_blocks)
+# Every shape the batch autotuner can pick (variant, CTA size, blocks per lane
+# in flight, tile size), plus odd CTA sizes and the defaults.
+SHAPES = [(1, th, tb, nb) for tb in (1024, 2048, 4096) for th in (256, 512, 1024) for nb in (1, 2, 4)] + \
+    [(2, 128, tb, 0) for tb in (1024, 2048, 4096)] + \
+    [(1, 1024, 8192, 2), (1, 256, 512, 1), (1, 544, 1024, 2), (2, 128, 256, 0), (0, 0, 2048, 0), (0, 0, 0, 0)]
+
+
+@pytest.mark.parametrize("variant,threads,tile_blocks,nb", SHAPES,
+                         ids=[f"v{v}_t{th}_tile{tb}_nb{nb}" for v, th, tb, nb in SHAPES])
+def test_mixed_batch_matches_oracle(cuda, aes, ncpu, variant, threads, tile_blocks, nb):
+    g = W.rng(40 + tile_blocks + threads + nb)
     lengths = mixed_lengths(g, 48)
     bits = [(128, 192, 256)[i % 3] for i in range(len(lengths))]
     kinds = [("random", "low32", "low64", "wrap128")[i % 4] for i in range(len(lengths))]
     reqs, meta, payload, src, dst = make_requests(cuda, aes, g, lengths, bits, kinds)
-    aes.batch(reqs, tile_blocks=tile_blocks, threads=threads)
+    aes.batch(reqs, variant=variant, tile_blocks=tile_blocks, threads=threads, blocks_per_thread=nb)
     check_all(cuda, meta, payload, dst, ncpu)
+
+
+def test_batch_autotune_picks_a_shape_that_stays_exact(cuda, aes, ncpu, tmp_path):
+    """aes_batch_autotune times every candidate shape on the caller's own
+    requests (overwriting their outputs with the correct ciphertext), makes
+    the fastest the device's batch shape, and batches that then use it (plans
+    and one-shot calls) still give the oracle's bytes."""
+    g = W.rng(47)
+    lengths = mixed_lengths(g, 40)
+    bits = [(128, 256)[i % 2] for i in range(len(lengths))]
+    reqs, meta, payload, src, dst = make_requests(cuda, aes, g, lengths, bits)
+    d = aes.batch_tuned_shape()
+    default = (d["variant"], d["threads"], d["tile_blocks"], d["blocks_per_thread"])
+    try:
+        best = aes.batch_autotune(reqs)
+        assert best == aes.batch_tuned_shape()
+        assert best["variant"] in (1, 2) and best["tile_blocks"] in (1024, 2048, 4096)
+        check_all(cuda, meta, payload, dst, ncpu)  # the candidates' own launches
+        dst.fill_(0xA5)
+        plan = aes.BatchPlan(reqs)
+        plan.launch()
+        check_all(cuda, meta, payload, dst, ncpu)
+        plan.close()
+        dst.fill_(0xA5)
+        aes.batch(reqs)
+        check_all(cuda, meta, payload, dst, ncpu)
+    finally:
+        set_batch_shape(cuda, aes, tmp_path / "shape.json", default)  # for the tests that follow
 
 
 @pytest.mark.parametrize("seed", [1, 7, 12345])

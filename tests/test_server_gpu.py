@@ -23,8 +23,25 @@ pytestmark = pytest.mark.gpu
 WAIT_US = 10_000_000
 
 
+@pytest.fixture(autouse=True, params=[0, 1], ids=["cursor", "per_request"])
+def claim_mode(request, monkeypatch, aes):
+    """Every test of this module runs under both tile-claim protocols of the
+    served kernel: the global cursor (claim_mode 0) and per-request claim
+    words (claim_mode 1).  Servers created without an explicit claim_mode
+    get the parametrised one."""
+    base = aes.Server
+
+    class ModeServer(base):
+        def __init__(self, *args, **kw):
+            kw.setdefault("claim_mode", request.param)
+            super().__init__(*args, **kw)
+
+    monkeypatch.setattr(aes, "Server", ModeServer)
+    return request.param
+
+
 @pytest.fixture()
-def server(aes):
+def server(aes, claim_mode):
     srv = aes.Server(slots=64, max_keys=16, ctas=32, tile_blocks=2048, idle_timeout_us=500_000)
     yield srv
     assert srv.close() == aes.AES_OK
@@ -662,7 +679,7 @@ def test_served_every_length_0_to_64(cuda, aes, ncpu, bits):
         assert srv.close() == aes.AES_OK
 
 
-def test_trace_build_stamps(cuda, aes):
+def test_trace_build_stamps(cuda, aes, claim_mode):
     """The trace build (libaesoffload_trace.so, built here) stamps each served
     request's steps, in protocol order.  Run as its own process
     (paper_2607_02630_gb300.served_trace), which loads that library instead
@@ -673,8 +690,10 @@ def test_trace_build_stamps(cuda, aes):
     import sys
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    r = subprocess.run([sys.executable, "-m", "paper_2607_02630_gb300.served_trace", "--requests", "40"],
+    r = subprocess.run([sys.executable, "-m", "paper_2607_02630_gb300.served_trace", "--requests", "40",
+                        "--claim-mode", str(claim_mode)],
                        capture_output=True, text=True, timeout=600, cwd=root)
     assert r.returncode == 0, r.stdout + r.stderr
     res = json.loads(r.stdout.strip().splitlines()[-1])
     assert res["ordered"] and res["median_us"]["done"] > 0, res
+    assert res["claim_mode"] == claim_mode
