@@ -245,6 +245,13 @@ int aes_batch_autotune(const aes_desc_t *descs, int n, void *stream, aes_batch_o
  * or the last aes_batch_autotune / aes_autotune / aes_autotune_load). */
 int aes_batch_tuned_shape(aes_batch_opts_t *out);
 
+/* The candidates of the last batch-shape sweep on the current device
+ * (aes_batch_autotune or aes_autotune) with their median launch times in ms
+ * (negative: the candidate did not run): up to `cap` entries into shapes[]
+ * and ms[].  Returns the number written (0 before any sweep), or
+ * AES_EINVAL. */
+int aes_batch_tune_results(aes_batch_opts_t *shapes, float *ms, int cap);
+
 /* Describe the shape AES_VARIANT_AUTO picks for (len, bits). */
 int aes_tuned_shape(size_t len, int bits, aes_launch_t *out);
 
@@ -307,7 +314,7 @@ typedef struct {
                                moved from request to request (default);
                                1 = per-request claim words that agents walk in
                                sequence order, several requests cut at once
-                               (experimental: not yet measured) */
+                               (same results; measured slower on GB300) */
     int trace_requests;     /* trace builds (libaesoffload_trace.so): keep timer
                                stamps of the protocol's steps for the last
                                trace_requests requests (a power of two up to

@@ -139,6 +139,8 @@ _SIGS = {
                                           ctypes.POINTER(BatchOpts)]),
     "aes_batch_tuned_shape": (ctypes.c_int, [ctypes.POINTER(BatchOpts)]),
     "aes_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks)]),
+    "aes_batch_tune_results": (ctypes.c_int, [ctypes.POINTER(BatchOpts), ctypes.POINTER(ctypes.c_float),
+                                              ctypes.c_int]),
     "aes_ctr_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.c_int, ctypes.c_void_p]),
     "offload_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ServerCfg)]),
     "offload_key_register": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -383,6 +385,14 @@ def batch_autotune(requests, stream=None) -> dict:
     _check(lib().aes_batch_autotune(arr, len(requests), stream_handle(stream), ctypes.byref(best)),
            "aes_batch_autotune")
     return _batch_opts_dict(best)
+
+
+def batch_tune_results() -> list:
+    """The last batch-shape sweep: [(shape dict, median ms), ...]."""
+    shapes = (BatchOpts * 64)()
+    ms = (ctypes.c_float * 64)()
+    n = _check(lib().aes_batch_tune_results(shapes, ms, 64), "aes_batch_tune_results")
+    return [(_batch_opts_dict(shapes[i]), float(ms[i])) for i in range(n)]
 
 
 def batch_tuned_shape() -> dict:

@@ -36,33 +36,28 @@ __device__ __forceinline__ uint32_t lds(const uint8_t *base, uint32_t o)
 }
 
 // Fill the replicated tables from Te0 (256 words in global memory).  Must be
-// followed by __syncthreads() before the first lookup.  Store q (16 bytes)
-// writes four lane copies of one entry; a thread issues the loads of eight
-// of its stores before any of the stores, so the fill waits for one L2 round
-// trip per eight stores rather than one per store (this fill is most of a
-// small launch's fixed cost).
+// followed by __syncthreads() before the first lookup.  Te0 is first staged
+// in a 1 KiB shared array (one global round trip for the whole CTA), then
+// store q (16 bytes) writes four lane copies of one entry, consecutive
+// threads writing consecutive 16-byte chunks (no bank conflicts; the staged
+// entry is a broadcast read for 16 consecutive stores).  The fill is most of
+// a short launch's fixed cost, so it waits for global memory only once.
 __device__ __forceinline__ void fill_tables(uint8_t *smem, const uint32_t *__restrict__ te0)
 {
+    __shared__ uint32_t s_te0[256];
+    for (uint32_t e = threadIdx.x; e < 256u; e += blockDim.x)
+        s_te0[e] = __ldg(te0 + e);
+    __syncthreads();
     constexpr uint32_t kStores = kTableBytes / 16;
-    for (uint32_t base = threadIdx.x; base < kStores; base += 8u * blockDim.x) {
-        uint32_t v[8];
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) {
-            const uint32_t q = base + k * blockDim.x;
-            v[k] = q < kStores ? __ldg(te0 + (((q & 4095u) * 4u) >> 6)) : 0u;  // entry e = word / 64
-        }
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) {
-            const uint32_t q = base + k * blockDim.x;
-            if (q >= kStores)
-                break;
-            const uint32_t h = q >> 12;              // region
-            const uint32_t w = (q & 4095u) * 4u;     // word index inside the region
-            const uint32_t t = (w >> 5) & 1u;        // even / odd table of the region
-            const uint32_t r = 8u * (2u * h + t);
-            const uint32_t val = r ? __funnelshift_l(v[k], v[k], r) : v[k];
-            *reinterpret_cast<uint4 *>(smem + h * kRegionBytes + w * 4u) = make_uint4(val, val, val, val);
-        }
+#pragma unroll 4
+    for (uint32_t q = threadIdx.x; q < kStores; q += blockDim.x) {
+        const uint32_t h = q >> 12;              // region
+        const uint32_t w = (q & 4095u) * 4u;     // word index inside the region
+        const uint32_t t = (w >> 5) & 1u;        // even / odd table of the region
+        const uint32_t r = 8u * (2u * h + t);
+        const uint32_t v = s_te0[w >> 6];        // entry e = word / 64
+        const uint32_t val = r ? __funnelshift_l(v, v, r) : v;
+        *reinterpret_cast<uint4 *>(smem + h * kRegionBytes + w * 4u) = make_uint4(val, val, val, val);
     }
 }
 

@@ -28,6 +28,12 @@ struct DeviceState {
     cudaStream_t setup = nullptr;   // internal non-blocking stream
     CtrShape ctr_tuned[3][kLenBuckets];  // [nr index: 10/12/14][length bucket]
     BatchShape batch_tuned;
+    // the last batch-shape sweep: every candidate and its median launch time
+    // (ms; negative if it did not run)
+    static constexpr int kMaxBatchCandidates = 64;
+    int n_batch_results = 0;
+    BatchShape batch_results[kMaxBatchCandidates];
+    float batch_results_ms[kMaxBatchCandidates];
 };
 
 extern thread_local char g_last_error[256];

@@ -51,9 +51,19 @@ constexpr uint32_t kRing = 64;  // >= workers + prefetch
 // next (8 MiB AES-256 stream: 440 GB/s with 1 queued tile, 664 with 16).
 constexpr uint32_t kPrefetch = 16;
 constexpr uint32_t kMaxClaim = 4;    // tiles per claim: spreads a request over many SMs
+// After an agent has claimed its fair share of a request (its tiles / the
+// CTA count, rounded up) it leaves the rest to other CTAs for up to this long
+// (ns), unless the cursor moves on: otherwise the first agents to see a new
+// request queue its tiles behind their own busy workers while other SMs sit
+// idle (one 1 MiB request: 512 tiles finished in 2-3 rounds on ~35 SMs).
+constexpr uint32_t kShareHoldNs = 2000;
 constexpr uint32_t kLookahead = 8;   // requests validated ahead of the cursor
 constexpr uint32_t kDispRing = 64;   // > kLookahead
 constexpr uint32_t kDispatchBatch = 4;  // queue entries read per round trip over the host link
+// Time limit of an idle worker's suspended wait for its ring slot (ns): the
+// wait ends early when the slot is filled; at the limit the worker looks at
+// the agent's exit code and waits again.
+constexpr uint32_t kWaitHintNs = 2000;
 // Per-request claims (claim_mode 1): a request's claim word holds its
 // sequence number above a 36-bit tile counter, so claims that overshoot the
 // tile count never reach the sequence bits; disp carries a busy bit while
@@ -65,7 +75,7 @@ constexpr uint64_t kDispBusy = 1ull << 40;
 struct QEntry {  // 64 bytes, host-written into the request's slot before its order word
     uint64_t tag;  // sequence number + 1 (informational)
     uint64_t in, out, len, iv_hi, iv_lo, gen;
-    uint32_t key_slot;
+    uint32_t key_slot;  // key slot (bits 0..23) | Nr of its key (bits 24..31; 0 = not registered)
     uint16_t desc;   // slot index d
     uint16_t flags;  // kFlagHostOut, kFlagEmulated
 };
@@ -93,7 +103,6 @@ struct SrvParams {
     unsigned long long *disp_ring; // kDispRing: ring_entry() of dispatched request s at s % kDispRing
     SrvRec *recs;
     const uint4 *keys;          // max_keys x 15 round keys
-    const int *key_nr;          // max_keys; 0 = unregistered
     const QEntry *queue;        // mapped: the body of the request in slot d at queue[d]
     const uint64_t *order;      // mapped: order[s & qmask] = ((s + 1) << 16) | d, stored after the body
     unsigned long long *done;   // mapped
@@ -101,6 +110,7 @@ struct SrvParams {
     unsigned int *kstatus;      // mapped
     const uint32_t *te0;
     uint32_t qmask, max_keys, tile_blocks, nslots;  // tile_blocks 0 = chosen per request
+    uint32_t nctas;             // resident CTAs (the fair share of a request is its tiles / nctas)
     uint64_t idle_ns, max_len;
     unsigned long long *trace;  // trace builds: kTracePoints stamps per request (null: off)
     uint32_t trace_mask;        // requests kept in the trace buffer - 1 (a power of two - 1)
@@ -153,6 +163,16 @@ SRV_INLINE T ld_cg(const T *p)
 }
 SRV_INLINE unsigned long long atom_add(unsigned long long *p, unsigned long long v) { return atomicAdd(p, v); }
 SRV_INLINE unsigned int atom_add(unsigned int *p, unsigned int v) { return atomicAdd(p, v); }
+// add with acquire-release semantics at GPU scope: the caller's earlier
+// stores (and those it has observed) are ordered before the add, and the
+// adds of other threads that precede it in the word's order before what
+// follows it
+SRV_INLINE unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 SRV_INLINE unsigned long long atom_cas(unsigned long long *p, unsigned long long c, unsigned long long v)
 {
     return atomicCAS(p, c, v);
@@ -336,6 +356,12 @@ inline unsigned int atom_add(unsigned int *p, unsigned int v)
     drain_address(p);
     return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL);
 }
+inline unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v)
+{
+    chaos();
+    drain_stores();  // a release: every earlier store of this thread is visible first
+    return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL);
+}
 inline unsigned long long atom_cas(unsigned long long *p, unsigned long long c, unsigned long long v)
 {
     chaos();
@@ -466,8 +492,12 @@ SRV_INLINE uint64_t ring_entry(uint32_t k, uint32_t d, uint32_t ntiles)
 // PER_REQ (claim_mode 1): the caller holds the dispatch lock (disp = k0 |
 // kDispBusy), so there is no CAS here, and each record's claim word is set
 // with its tile count.
+// pre_ow (optional): the order words of k0 .. k0 + kDispatchBatch - 1,
+// already loaded (relaxed) by the caller, e.g. by the advancer's polling
+// loop, so a request seen there costs no second read of its order word.
 template <bool PER_REQ>
-SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, uint64_t *first = nullptr)
+SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, uint64_t *first = nullptr,
+                               const uint64_t *pre_ow = nullptr)
 {
     // The order words name each request's slot; its body sits in the slot,
     // which the request holds until it completes, so the body cannot change
@@ -476,18 +506,20 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
     uint64_t ow[kDispatchBatch];
 #pragma unroll
     for (uint32_t i = 0; i < kDispatchBatch; ++i)
-        ow[i] = i < n_max ? ld_relaxed_sys(p.order + ((k0 + i) & p.qmask)) : 0;
+        ow[i] = i >= n_max ? 0 : pre_ow ? pre_ow[i] : ld_relaxed_sys(p.order + ((k0 + i) & p.qmask));
 #pragma unroll
     for (uint32_t i = 0; i < kDispatchBatch; ++i)
         if (m == i && i < n_max && (uint32_t)((ow[i] >> 16) & kSeqMask) == ((k0 + i + 1) & kSeqMask))
             m = i + 1;
     if (m == 0)
         return 0;
+#ifdef SRV_TRACE
+    const uint64_t t_seen = gtime();
+#endif
     fence_acq_rel_sys();
-    if (!PER_REQ && atom_cas(p.disp, (unsigned long long)k0, (unsigned long long)((k0 + m) & kSeqMask)) != k0)
-        return 0;
-    for (uint32_t i = 0; i < m; ++i)
-        trace(p, (k0 + i) & kSeqMask, kTrDispatch);
+    // The bodies are read before the requests are claimed (CAS on disp), so
+    // the host-link reads and the claim in L2 are in flight together; a
+    // dispatcher that loses the claim drops what it read.
     uint64_t x[kDispatchBatch][7];
 #pragma unroll
     for (uint32_t i = 0; i < kDispatchBatch; ++i) {
@@ -501,6 +533,13 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
             (void)unused;
         }
     }
+    if (!PER_REQ && atom_cas(p.disp, (unsigned long long)k0, (unsigned long long)((k0 + m) & kSeqMask)) != k0)
+        return 0;
+#ifdef SRV_TRACE
+    for (uint32_t i = 0; i < m; ++i)
+        if (p.trace)
+            p.trace[(size_t)(((k0 + i) & kSeqMask) & p.trace_mask) * kTracePoints + kTrDispatch] = t_seen;
+#endif
     uint64_t ent[kDispatchBatch] = {};
     uint32_t done_word[kDispatchBatch] = {};  // status for a request completed here, else 0
 #pragma unroll
@@ -509,7 +548,8 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
             continue;
         const uint32_t k = (k0 + i) & kSeqMask;
         const uint64_t in = x[i][0], out = x[i][1], len = x[i][2], iv_hi = x[i][3], iv_lo = x[i][4];
-        const uint32_t ks = (uint32_t)x[i][6];
+        const uint32_t ks = (uint32_t)x[i][6] & 0xffffffu;
+        const uint32_t key_nr = ((uint32_t)x[i][6] >> 24) & 0xffu;  // the host's record of the key's Nr
         const uint32_t d = (uint32_t)(ow[i] & 0xffffu);
         const uint32_t flags = (uint32_t)(x[i][6] >> 48);
         done_word[i] = 0;
@@ -517,9 +557,7 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
             ent[i] = ring_entry(k, 0xffffu, 0);
             continue;
         }
-        int nr = 0;
-        if (ks < p.max_keys)
-            nr = ld_cg(p.key_nr + ks);
+        int nr = ks < p.max_keys ? (int)key_nr : 0;
         bool ok = (nr == 10 || nr == 12 || nr == 14) && len <= p.max_len;
         if (ok && len)
             ok = in && out && !((in | out) & 15u);
@@ -562,15 +600,19 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
         st_field(&rec->tile_groups, tg);
         st_field(&rec->tile_parts, tp);
         ent[i] = ring_entry(k, d, ntiles);
-        if (PER_REQ)  // with the record: a claim that sees the claim word below finds it
-            st_relaxed_gpu(&rec->seq_ntiles, ((uint64_t)k << kTileBits) | ntiles);
+        // with the record: a claim finds it once it has seen the ring entry
+        // (global cursor) or the claim word (per-request claims) below
+        st_relaxed_gpu(&rec->seq_ntiles, ((uint64_t)k << kTileBits) | ntiles);
         if (ntiles == 0)
             done_word[i] = ok ? 1u : 2u;
     }
+    // One fence: the ring entries (and with per-request claims the claim
+    // words) follow the records.  Nothing reads a record's seq_ntiles for
+    // request k before it has seen k's ring entry or claim word: the cursor
+    // names k only after the advancer has read k's ring entry.
     fence_gpu();
     if (PER_REQ) {
-        // One fence: the claim word and the ring entry follow the record.  A
-        // claimer that sees the ring entry before the claim word retries
+        // A claimer that sees the ring entry before the claim word retries
         // (it reads an older sequence number there).
 #pragma unroll
         for (uint32_t i = 0; i < kDispatchBatch; ++i) {
@@ -578,14 +620,6 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
             if (i < m && d != 0xffffu)
                 st_relaxed_gpu(&p.recs[d].claim, (ent[i] >> 36) << kClaimShift);
         }
-    } else {
-#pragma unroll
-        for (uint32_t i = 0; i < kDispatchBatch; ++i) {
-            const uint32_t d = (uint32_t)(ent[i] >> kTileBits) & 0xffffu;
-            if (i < m && d != 0xffffu)
-                st_relaxed_gpu(&p.recs[d].seq_ntiles, ((ent[i] >> 36) << kTileBits) | (ent[i] & kTileMask));
-        }
-        fence_gpu();
     }
     for (uint32_t i = 0; i < m; ++i)  // before the ring entries: no claim can precede it
         trace(p, (k0 + i) & kSeqMask, kTrPublished);
@@ -607,25 +641,62 @@ SRV_NOINLINE uint32_t dispatch(const SrvParams &p, uint32_t k0, uint32_t n_max, 
     return m;
 }
 
+SRV_INLINE void dispatch_ahead(const SrvParams &p, uint32_t nseq)
+{
+    const uint32_t k = (uint32_t)ld_relaxed_gpu(p.disp);
+    const uint32_t ahead = (k - nseq) & kSeqMask;
+    if (ahead <= kLookahead)
+        dispatch<false>(p, k, kLookahead + 1 - ahead);
+}
+
+// What an agent remembers between global-cursor claims, to save round trips
+// to L2: the (sequence, slot) of its last successful claim with that
+// request's seq_ntiles word (valid while its claims keep landing on the same
+// request; dropped after any failed claim), and a cursor value it has just
+// seen move to a new request, whose seq_ntiles it loads alongside its next
+// claim instead of after it.
+struct ClaimCache {
+    uint64_t key = ~0ull;  // (seq << 16) | slot of the cached seq_ntiles
+    uint64_t sn = 0;
+    uint64_t seen = ~0ull; // (seq << 16) | slot the cursor was seen to name
+    uint32_t lookahead = 0;  // nonzero: validate requests ahead of this sequence number once the claimed tiles are queued
+};
+
 // Elected advancer (adv has been moved from seq to seq + 1): move the cursor
 // to request seq + 1 once its dispatch-ring entry is published (dispatching
 // it, with what is queued behind it, if it is next in line), step over
 // requests without tiles, and dispatch up to kLookahead requests ahead.
 // With block == false the role is handed back at once (kNotReady) when the
-// next request is not ready.  Returns 0, kNotReady or an exit code (after
-// handing the role back).
-SRV_NOINLINE uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_work, StopCheck &stop,
-                                        bool block)
+// next request is not ready.  With reserve > 0 the cursor move itself claims
+// the new request's first `reserve` tiles for the caller: *got is set to
+// their count (0 if it moved to no request with tiles) with the request's
+// slot, sequence number and tile count in *rd, *rseq, *rnt.  Returns 0,
+// kNotReady or an exit code (after handing the role back).
+SRV_NOINLINE uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_work, StopCheck &stop, bool block,
+                              ClaimCache &cache, uint32_t reserve = 0, uint32_t *got = nullptr,
+                              uint32_t *rd = nullptr, uint32_t *rseq = nullptr, uint32_t *rnt = nullptr)
 {
+    if (got)
+        *got = 0;
     for (;;) {
         const uint32_t nseq = (seq + 1) & kSeqMask;
         uint64_t e = 0;
-        for (;;) {
+        for (uint32_t round = 0;; ++round) {
+            // The ring entry and the dispatch word in L2; from the second
+            // round on (waiting for a request: polling), the next order words
+            // over the host link in the same round of loads.  Under load the
+            // entry is usually published already, and the first round finds
+            // it without a host-link round trip.
             e = ld_relaxed_gpu(p.disp_ring + (nseq % kDispRing));
+            const uint32_t dsp = (uint32_t)ld_relaxed_gpu(p.disp);
+            uint64_t ow[kDispatchBatch];
+            if (round)
+#pragma unroll
+                for (uint32_t i = 0; i < kDispatchBatch; ++i)
+                    ow[i] = ld_relaxed_sys(p.order + ((nseq + i) & p.qmask));
             if ((uint32_t)(e >> 36) == nseq)
                 break;  // dispatched and published
-            const uint32_t dsp = (uint32_t)ld_relaxed_gpu(p.disp);
-            if (dsp == nseq && dispatch<false>(p, nseq, kLookahead + 1, &e))
+            if (dsp == nseq && dispatch<false>(p, nseq, kLookahead + 1, &e, round ? ow : nullptr))
                 break;  // dispatched it here: e is its ring entry
             uint32_t r = 0;
             if (!block)
@@ -643,15 +714,29 @@ SRV_NOINLINE uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_w
         const uint32_t d = (uint32_t)(e >> kTileBits) & 0xffffu;
         if (d >= p.nslots)
             return kExitError;
+        const uint32_t nt = (uint32_t)(e & kTileMask);
         // Only the elected advancer changes the sequence number; claims that
-        // raced with it only added to the tile count of the old request.
-        atom_exch(p.cursor, ((unsigned long long)nseq << 36) | ((unsigned long long)d << kTileBits));
+        // raced with it only added to the tile count of the old request.  The
+        // ring entry carries the request's tile count, so the caller's first
+        // claim (made by this very store when reserving) needs no record read.
+        const uint32_t take = reserve && nt ? reserve : 0u;
+        atom_exch(p.cursor, ((unsigned long long)nseq << 36) | ((unsigned long long)d << kTileBits) | take);
+        cache.key = ((uint64_t)nseq << 16) | d;
+        cache.sn = ((uint64_t)nseq << kTileBits) | nt;
         last_work = gtime();
-        const uint32_t k = (uint32_t)ld_relaxed_gpu(p.disp);
-        const uint32_t ahead = (k - nseq) & kSeqMask;
-        if (ahead <= kLookahead)
-            dispatch<false>(p, k, kLookahead + 1 - ahead);
-        if (e & kTileMask)
+        if (take) {
+            // the caller queues its tiles first; the look-ahead dispatch
+            // (a round trip over the host link) waits until they are queued
+            *got = take < nt ? take : nt;
+            *rd = d;
+            *rseq = nseq;
+            *rnt = nt;
+            trace(p, nseq, kTrFirstClaim);
+            cache.lookahead = nseq | 0x80000000u;
+            return 0;
+        }
+        dispatch_ahead(p, nseq);
+        if (nt)
             return 0;
         // nothing to claim in nseq: step over it, unless another agent
         // (which saw the empty request) already took that role
@@ -664,20 +749,36 @@ SRV_NOINLINE uint32_t advance(const SrvParams &p, uint32_t seq, uint64_t &last_w
 // Claim up to `want` tiles of the current request (the agent of a CTA).
 // Returns 0 with the tiles [*t0, *t1) of slot *d and its sequence number, or
 // an exit code.
-SRV_FN uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &stop, uint32_t want,
-                          uint32_t *d_out, uint32_t *seq_out, uint32_t *t0, uint32_t *t1, uint32_t *nt_out)
+// idle_workers: this CTA's workers wait for tiles, so an agent that moves
+// the cursor takes the new request's first tiles in the same store (the
+// one-in-flight case); with work still queued it leaves them to the others.
+SRV_FN uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &stop, uint32_t want, bool idle_workers,
+                      uint32_t *d_out, uint32_t *seq_out, uint32_t *t0, uint32_t *t1, uint32_t *nt_out,
+                      ClaimCache &cache)
 {
     for (;;) {
         if (stop(p.stop))
             return kExitStop;
+        // the record word of a request the cursor was just seen to name is
+        // loaded together with the claim (both in flight at once)
+        uint64_t sn_seen = 0;
+        const uint64_t seen = cache.seen;
+        if (seen != ~0ull && (uint32_t)(seen & 0xffffu) < p.nslots)
+            sn_seen = ld_relaxed_gpu(&p.recs[seen & 0xffffu].seq_ntiles);
+        cache.seen = ~0ull;
         const unsigned long long v = atom_add(p.cursor, (unsigned long long)want);
         const uint32_t seq = (uint32_t)(v >> 36);
         const uint32_t d = (uint32_t)(v >> kTileBits) & 0xffffu;
         const uint32_t t = (uint32_t)v & kTileMask;
         if (d < p.nslots) {
-            const uint64_t sn = ld_relaxed_gpu(&p.recs[d].seq_ntiles);
+            const uint64_t key = ((uint64_t)seq << 16) | d;
+            const uint64_t sn = key == cache.key ? cache.sn
+                                : key == seen    ? sn_seen
+                                                 : ld_relaxed_gpu(&p.recs[d].seq_ntiles);
             const uint32_t nt = (uint32_t)(sn & kTileMask);
             if ((uint32_t)(sn >> kTileBits) == seq && t < nt) {
+                cache.key = key;
+                cache.sn = sn;
                 *d_out = d;
                 *seq_out = seq;
                 *t0 = t;
@@ -689,19 +790,33 @@ SRV_FN uint32_t claim(const SrvParams &p, uint64_t &last_work, StopCheck &stop, 
                 return 0;
             }
         }
-        // The current request has no tiles left: advance, or wait for the
-        // CTA that does.
+        cache.key = ~0ull;  // a failed claim: never reuse an older request's word
+        // The current request has no tiles left: advance (claiming the next
+        // request's first tiles in the same store), or wait for the CTA that
+        // does.
         if (atom_cas(p.adv, (unsigned long long)seq, (unsigned long long)((seq + 1) & kSeqMask)) == seq) {
-            const uint32_t r = advance(p, seq, last_work, stop, true);
+            uint32_t got = 0, rd = 0, rseq = 0, rnt = 0;
+            const uint32_t r = advance(p, seq, last_work, stop, true, cache, idle_workers ? want : 0u, &got, &rd,
+                                       &rseq, &rnt);
             if (r)
                 return r;
+            if (got) {
+                *d_out = rd;
+                *seq_out = rseq;
+                *t0 = 0;
+                *t1 = got;
+                *nt_out = rnt;
+                return 0;
+            }
         } else {
             for (uint32_t spin = 0;; ++spin) {
-                if ((uint32_t)(ld_relaxed_gpu(p.cursor) >> 36) != seq) {
+                const uint64_t c = ld_relaxed_gpu(p.cursor);
+                if ((uint32_t)(c >> 36) != seq) {
                     // the server is working even if this CTA's claims keep
                     // losing: idle means no new request anywhere, so a CTA
                     // does not exit under light load while others serve
                     last_work = gtime();
+                    cache.seen = (c >> kTileBits) & ((1ull << 44) - 1);  // (seq << 16) | slot
                     break;
                 }
                 if ((spin & 7) == 7 && (uint32_t)ld_relaxed_gpu(p.adv) == seq)
@@ -910,13 +1025,12 @@ SRV_FN uint32_t claim_pr(const SrvParams &p, uint32_t &cur, uint64_t &last_work,
 // the cursor is moved on once they are queued (lease_queued).
 template <bool PER_REQ>
 SRV_INLINE uint32_t agent_claim(const SrvParams &p, uint32_t &cur, uint64_t &last_work, StopCheck &stop,
-                                uint32_t want, uint32_t *d, uint32_t *seq, uint32_t *t0, uint32_t *t1,
-                                bool &adv_after)
+                                uint32_t want, bool idle_workers, uint32_t *d, uint32_t *seq, uint32_t *t0,
+                                uint32_t *t1, uint32_t *nt, bool &adv_after, ClaimCache &cache)
 {
-    uint32_t nt = 0;
-    const uint32_t code = PER_REQ ? claim_pr(p, cur, last_work, stop, want, d, seq, t0, t1, &nt)
-                                  : claim(p, last_work, stop, want, d, seq, t0, t1, &nt);
-    adv_after = !PER_REQ && code == 0 && *t1 == nt;
+    const uint32_t code = PER_REQ ? claim_pr(p, cur, last_work, stop, want, d, seq, t0, t1, nt)
+                                  : claim(p, last_work, stop, want, idle_workers, d, seq, t0, t1, nt, cache);
+    adv_after = !PER_REQ && code == 0 && *t1 == *nt;
     return code;
 }
 
@@ -927,72 +1041,217 @@ SRV_INLINE uint32_t agent_claim(const SrvParams &p, uint32_t &cur, uint64_t &las
 // ready).  Returns 0 or an exit code.
 template <bool PER_REQ>
 SRV_INLINE uint32_t lease_queued(const SrvParams &p, uint32_t cur, uint32_t lseq, bool &adv_after,
-                                 uint64_t &last_work, StopCheck &stop)
+                                 uint64_t &last_work, StopCheck &stop, ClaimCache &cache)
 {
     if (PER_REQ) {
         lookahead(p, cur);
         return 0;
     }
+    if (cache.lookahead) {  // the advancer's look-ahead, postponed until its tiles were queued
+        dispatch_ahead(p, cache.lookahead & 0x7fffffffu);
+        cache.lookahead = 0;
+    }
     if (!adv_after)
         return 0;
     adv_after = false;
     if (atom_cas(p.adv, (unsigned long long)lseq, (unsigned long long)((lseq + 1) & kSeqMask)) == lseq) {
-        const uint32_t r = advance(p, lseq, last_work, stop, false);
+        const uint32_t r = advance(p, lseq, last_work, stop, false, cache);
         if (r && r != kNotReady)
             return r;
     }
     return 0;
 }
 
-// A worker finished one tile of the request in slot d; the worker finishing
-// the last one raises the request's completion word in host memory
-// (system-scope release after a system-scope fence over its output stores).
-SRV_INLINE void tile_finished(const SrvParams &p, uint32_t d)
+// A worker finished one tile of request seq (in slot d, ntiles tiles,
+// generation gen); the worker finishing the last one raises the request's
+// completion word in host memory.  Ordering: each worker's tile stores come
+// before its acquire-release add on done_tiles (the worker's lane 0 adds
+// after a warp barrier over the tile's stores; for host-memory outputs the
+// warp has also fenced at system scope); the last add acquires every
+// earlier one, and the completion word is stored with system-scope release,
+// so a host that sees the word sees every tile's output.
+SRV_INLINE void tile_finished(const SrvParams &p, uint32_t d, uint32_t ntiles, uint32_t seq, uint64_t gen)
 {
     SrvRec *rec = p.recs + d;
-    const uint64_t sn = ld_relaxed_gpu(&rec->seq_ntiles);
-    const uint32_t ntiles = (uint32_t)(sn & kTileMask);
-    const unsigned int prev = atom_add(&rec->done_tiles, 1u);
+    const unsigned int prev = atom_add_acq_rel(&rec->done_tiles, 1u);
     if (prev + 1 == ntiles) {
-        fence_sys();
-        trace(p, (uint32_t)(sn >> kTileBits), kTrDone);
-        st_release_sys(p.done + d, (ld_cg(&rec->gen) << 2) | 1u);
+        trace(p, seq, kTrDone);
+        st_release_sys(p.done + d, (gen << 2) | 1u);
     }
+    (void)seq;
 }
 
 
 // ---- the CTA: agent and worker warps, joined by a ring in shared memory ----
-// The agent (warp 0, lane 0) claims tiles and pushes them; each worker warp's
-// lane 0 reserves the next position (atomicAdd on head) and waits for the
-// agent to fill it.  A slot is refilled only once the worker that read its
-// previous item has marked it read.
+// The agent (warp 0, lane 0) claims tiles and pushes them; each worker warp
+// reserves the next position (atomicAdd on head) and waits for the agent to
+// fill it.  A slot is refilled only once the worker that read its previous
+// item has marked it read.  On the GPU each slot has an mbarrier whose phase
+// completes when the agent fills it, so waiting workers are suspended in
+// mbarrier.try_wait instead of polling shared memory (a polling warp takes
+// issue slots and shared-memory cycles from the warps that encrypt: with 14
+// idle workers polling, the one encrypting ran 3.5x slower); host builds
+// poll.
+//
+// The worker that reserved a position writes (position << 8) | its warp into
+// the slot's owner word, so the agent can see on which SM partition (warp %
+// 4) each waiting worker runs: when the next waiting worker's partition
+// already runs a tile of the same lease and a later waiting worker's does
+// not, the agent fills the position with an empty item (the worker reserves
+// again) and gives the tile to the later one.  The tiles of one claim then
+// run on different partitions instead of sharing one partition's issue slot
+// (two tiles on one partition take 1.6x as long, three 2.2x).  Under load no
+// worker waits and the agent fills in order.
 struct Ring {
+#ifdef __CUDACC__
+    unsigned long long full[kRing];  // mbarrier per slot, expected arrivals 1 (device builds)
+#endif
     unsigned int head;               // positions reserved by workers (atomicAdd)
     volatile unsigned int tail;      // positions filled by the agent
     volatile unsigned int exit_code; // set by the agent after its last push
-    uint32_t d[kRing], t[kRing], seq[kRing];
+    uint32_t d[kRing], t[kRing], seq[kRing], nt[kRing];  // nt == 0: an empty item
     volatile unsigned int read_mark[kRing];  // position + 1 of the last item read from each slot
+    volatile unsigned int owner[kRing];      // (position << 8) | warp of the worker that reserved it
 };
+constexpr uint32_t kPartitions = 4;  // warp w of an SM runs on partition w % 4
 
-// Agent warp, lane 0: keep the ring kPrefetch items ahead of the workers.
-// PER_REQ selects per-request claims (claim_mode 1) over the global cursor.
+#ifdef __CUDACC__
+SRV_INLINE uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// The agent filled `slot`: complete the slot's current phase (release: the
+// item's fields are visible to the worker whose wait sees the phase end).
+SRV_INLINE void ring_signal(Ring &ring, uint32_t slot)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&ring.full[slot]))
+                 : "memory");
+}
+// Wait (suspended, up to about hint_ns) for the phase of `slot` with the
+// given parity to complete; true once it has (acquire).
+SRV_INLINE bool ring_try_wait(Ring &ring, uint32_t slot, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 P1, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, P1;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(&ring.full[slot])), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+#else
+inline void ring_signal(Ring &, uint32_t) {}
+#endif
+
+// The ring's counters, set by one thread before the agent and the workers
+// start (and its barriers initialised on the GPU).
+SRV_INLINE void ring_init(Ring &ring)
+{
+    ring.head = 0;
+    ring.tail = 0;
+    ring.exit_code = 0;
+    for (uint32_t i = 0; i < kRing; ++i) {
+        ring.read_mark[i] = 0;
+        ring.owner[i] = ~0u;
+    }
+#ifdef __CUDACC__
+    for (uint32_t i = 0; i < kRing; ++i)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&ring.full[i])) : "memory");
+#endif
+}
+
+// How many items the agent may add now: slots whose previous item has been
+// read, up to kPrefetch queued beyond the waiting workers.  *waiting:
+// workers waiting for an item.
+SRV_INLINE uint32_t ring_room(Ring &ring, uint32_t *waiting)
+{
+    const uint32_t head = ld_vol(reinterpret_cast<volatile unsigned int *>(&ring.head));
+    const uint32_t tail = ld_vol(&ring.tail);
+    const int32_t queued = (int32_t)(tail - head);
+    *waiting = queued < 0 ? (uint32_t)(-queued) : 0u;
+    const uint32_t want = queued < (int32_t)kPrefetch ? (uint32_t)((int32_t)kPrefetch - queued) : 0u;
+    uint32_t r = 0;
+    while (r < want && r < 2 * kMaxClaim &&
+           (tail + r < kRing || ld_vol(&ring.read_mark[(tail + r) % kRing]) == tail + r - kRing + 1))
+        ++r;
+    return r;
+}
+
+// The partition of the worker waiting at position pos, or kPartitions when
+// unknown (its owner word is not written yet).
+SRV_INLINE uint32_t ring_owner_partition(Ring &ring, uint32_t pos)
+{
+    const uint32_t o = ld_vol(&ring.owner[pos % kRing]);
+    return (o >> 8) == (pos & 0xffffffu) ? (o & 0xffu) % kPartitions : kPartitions;
+}
+
+// Queue tiles [lt, lend) of a lease into up to `room` positions: the items'
+// fields (empty items where a waiting worker's partition already runs a tile
+// of this lease and a later waiting worker's is free; `used` holds the
+// lease's partitions), one CTA fence, the new tail, then each filled slot's
+// barrier.  Returns the number of tiles queued.
+SRV_INLINE uint32_t push_lease(Ring &ring, uint32_t room, uint32_t d, uint32_t seq, uint32_t lt, uint32_t lend,
+                               uint32_t nt, uint32_t &used)
+{
+    const uint32_t tail = ld_vol(&ring.tail);
+    const uint32_t head = ld_vol(reinterpret_cast<volatile unsigned int *>(&ring.head));
+    uint32_t filled = 0, tiles = 0;
+    while (filled < room && lt + tiles < lend) {
+        const uint32_t pos = tail + filled;
+        const uint32_t slot = pos % kRing;
+        bool skip = false;
+        if ((int32_t)(head - pos) > 0) {  // a worker waits at pos
+            const uint32_t part = ring_owner_partition(ring, pos);
+            if (part < kPartitions && ((used >> part) & 1u)) {
+                for (uint32_t q = pos + 1; (int32_t)(head - q) > 0 && q < tail + room; ++q) {
+                    const uint32_t pq = ring_owner_partition(ring, q);
+                    if (pq < kPartitions && !((used >> pq) & 1u)) {
+                        skip = true;
+                        break;
+                    }
+                }
+            }
+            if (!skip && part < kPartitions)
+                used |= 1u << part;
+        }
+        st_field(&ring.d[slot], d);
+        st_field(&ring.t[slot], lt + tiles);
+        st_field(&ring.seq[slot], seq);
+        st_field(&ring.nt[slot], skip ? 0u : nt);
+        ++filled;
+        if (!skip)
+            ++tiles;
+    }
+    if (filled) {
+        fence_cta();
+        st_vol(&ring.tail, tail + filled);
+        for (uint32_t i = 0; i < filled; ++i)
+            ring_signal(ring, (tail + i) % kRing);
+    }
+    return tiles;
+}
+
+// Agent warp, lane 0: keep the ring up to kPrefetch items ahead of the
+// workers.  PER_REQ selects per-request claims (claim_mode 1) over the
+// global cursor.
 template <bool PER_REQ>
 SRV_NOINLINE void agent(const SrvParams &p, Ring &ring)
 {
     uint64_t last_work = gtime();
     StopCheck stop;
+    ClaimCache cache;
     uint32_t cur = PER_REQ ? (uint32_t)ld_relaxed_gpu(p.cursor) : 0u;  // request this agent stands on
-    uint32_t ld = 0, lseq = 0, lt = 0, lend = 0;  // current lease: tiles [lt, lend) of slot ld
-    bool adv_after = false;                      // the lease ends its request
+    uint32_t ld = 0, lseq = 0, lt = 0, lend = 0, lnt = 0;  // current lease: tiles [lt, lend) of slot ld
+    uint32_t lparts = 0;                                  // partitions running the current lease's tiles
+    bool adv_after = false;                               // the lease ends its request
     uint32_t code = 0;
     uint32_t backoff = 32;  // ns; a spinning agent would take shared-memory cycles from its workers
+    // global cursor: the request this agent last claimed from, how many of its
+    // tiles it took, its fair share and when the share was reached
+    uint32_t fs_seq = ~0u, fs_taken = 0, fs_share = ~0u, fs_nt = 0;
+    uint64_t fs_full_at = 0;
     for (;;) {
-        const uint32_t head = ld_vol(reinterpret_cast<volatile unsigned int *>(&ring.head));
-        const uint32_t tail = ld_vol(&ring.tail);
-        // full: kPrefetch items already wait for workers, or the item that
-        // position tail would overwrite (tail - kRing) has not been read yet
-        if ((int32_t)(tail - head) >= (int32_t)kPrefetch ||
-            (tail >= kRing && ld_vol(&ring.read_mark[tail % kRing]) != tail - kRing + 1)) {
+        uint32_t waiting = 0;
+        const uint32_t room = ring_room(ring, &waiting);
+        if (!room) {  // full
             if (stop(p.stop)) {
                 code = kExitStop;
                 break;
@@ -1002,22 +1261,44 @@ SRV_NOINLINE void agent(const SrvParams &p, Ring &ring)
             continue;
         }
         if (lt >= lend) {
-            const uint32_t waiting = (int32_t)(head - tail) > 0 ? head - tail : 0u;
+            if (!PER_REQ && fs_taken >= fs_share) {
+                // this CTA holds its share of request fs_seq: while the cursor is
+                // still on it with tiles left, give the other CTAs kShareHoldNs
+                const uint64_t cv = ld_relaxed_gpu(p.cursor);
+                if ((uint32_t)(cv >> 36) == fs_seq && ((uint32_t)cv & kTileMask) < fs_nt &&
+                    since(fs_full_at) < (int64_t)kShareHoldNs) {
+                    if (stop(p.stop)) {
+                        code = kExitStop;
+                        break;
+                    }
+                    nap(64);
+                    continue;
+                }
+                fs_share = ~0u;  // hold over: claim as usual
+            }
             const uint32_t want = waiting + kPrefetch < kMaxClaim ? waiting + kPrefetch : kMaxClaim;
-            code = agent_claim<PER_REQ>(p, cur, last_work, stop, want, &ld, &lseq, &lt, &lend, adv_after);
+            code = agent_claim<PER_REQ>(p, cur, last_work, stop, want, waiting > 0, &ld, &lseq, &lt, &lend, &lnt,
+                                        adv_after, cache);
             if (code)
                 break;
+            lparts = 0;
+            if (!PER_REQ) {
+                if (lseq != fs_seq) {
+                    fs_seq = lseq;
+                    fs_taken = 0;
+                    fs_nt = lnt;
+                    fs_share = p.nctas ? (lnt + p.nctas - 1) / p.nctas : ~0u;
+                }
+                fs_taken += lend - lt;
+                if (fs_taken >= fs_share)
+                    fs_full_at = gtime();
+            }
         }
-        const uint32_t slot = tail % kRing;
-        st_field(&ring.d[slot], ld);
-        st_field(&ring.t[slot], lt);
-        st_field(&ring.seq[slot], lseq);
-        ++lt;
+        // the room seen before the claim is still available: only the agent fills
+        lt += push_lease(ring, room, ld, lseq, lt, lend, lnt, lparts);
         backoff = 32;
-        fence_cta();
-        st_vol(&ring.tail, tail + 1);
         if (lt >= lend) {  // the whole lease is queued
-            code = lease_queued<PER_REQ>(p, cur, lseq, adv_after, last_work, stop);
+            code = lease_queued<PER_REQ>(p, cur, lseq, adv_after, last_work, stop, cache);
             if (code)
                 break;
         }
@@ -1026,12 +1307,14 @@ SRV_NOINLINE void agent(const SrvParams &p, Ring &ring)
     st_vol(&ring.exit_code, code);
 }
 
-// A worker warp's lane 0: take the next position and wait for the agent to
-// fill it.  Returns false when the agent has exited without filling it (its
-// last pushes are taken first).
-SRV_INLINE bool ring_pop(Ring &ring, uint32_t *d, uint32_t *t, uint32_t *seq)
+// A worker's lane 0 (host builds): take the next position and wait for the
+// agent to fill it.  Returns false when the agent has exited without filling
+// it (its last pushes are taken first).
+SRV_INLINE bool ring_pop(Ring &ring, uint32_t warp, uint32_t *d, uint32_t *t, uint32_t *seq, uint32_t *nt)
 {
+again:
     const uint32_t pos = atom_add(&ring.head, 1u);
+    st_vol(&ring.owner[pos % kRing], (pos << 8) | warp);
     for (uint32_t spin = 0;; ++spin) {
         if ((int32_t)(ld_vol(&ring.tail) - pos) > 0)
             break;
@@ -1048,9 +1331,55 @@ SRV_INLINE bool ring_pop(Ring &ring, uint32_t *d, uint32_t *t, uint32_t *seq)
     *d = ld_field(&ring.d[pos % kRing]);
     *t = ld_field(&ring.t[pos % kRing]);
     *seq = ld_field(&ring.seq[pos % kRing]);
+    *nt = ld_field(&ring.nt[pos % kRing]);
     fence_cta();
     st_vol(&ring.read_mark[pos % kRing], pos + 1);
+    if (*nt == 0)
+        goto again;  // an empty item: the tile went to another partition
     return true;
 }
+
+#ifdef __CUDACC__
+// The same step for a whole worker warp on the GPU: lane 0 reserves the
+// position; the warp waits suspended on the slot's mbarrier for the phase of
+// this lap (position / kRing) -- at most 15 workers wait beyond the filled
+// positions and kRing = 64, so the slot's previous lap is always filled
+// before anyone waits for this one, and the parity names this lap alone.
+// The wait is re-armed every ~2 us to look at the agent's exit code.
+SRV_INLINE bool ring_pop_warp(Ring &ring, uint32_t *d, uint32_t *t, uint32_t *seq, uint32_t *nt)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+again:
+    uint32_t pos = 0;
+    if (lane == 0) {
+        pos = atomicAdd(&ring.head, 1u);
+        st_vol(&ring.owner[pos % kRing], (pos << 8) | (threadIdx.x >> 5));
+    }
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    const uint32_t slot = pos % kRing, parity = (pos / kRing) & 1u;
+    for (;;) {
+        const bool full = __shfl_sync(0xffffffffu, (uint32_t)ring_try_wait(ring, slot, parity, kWaitHintNs), 0) != 0;
+        if (full)
+            break;
+        if (ld_vol(&ring.exit_code)) {
+            __threadfence_block();
+            if ((int32_t)(ld_vol(&ring.tail) - pos) <= 0)
+                return false;  // the agent has left; this position was never filled
+        }
+    }
+    *d = ring.d[slot];
+    *t = ring.t[slot];
+    *seq = ring.seq[slot];
+    *nt = ring.nt[slot];
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        st_vol(&ring.read_mark[slot], pos + 1);
+    }
+    if (*nt == 0)
+        goto again;  // an empty item: the tile went to another partition
+    return true;
+}
+#endif
 
 }  // namespace srvp

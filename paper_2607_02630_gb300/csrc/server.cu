@@ -123,13 +123,8 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ Ring ring;
-    if (threadIdx.x == 0) {
-        ring.head = 0;
-        ring.tail = 0;
-        ring.exit_code = 0;
-        for (uint32_t i = 0; i < kRing; ++i)
-            ring.read_mark[i] = 0;
-    }
+    if (threadIdx.x == 0)
+        ring_init(ring);
     aestt::fill_tables(smem, p.te0);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -143,28 +138,33 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
     }
     const aestt::Lanes ln;
     uint32_t cur_d = ~0u, cur_seq = ~0u, tg = 1, tp = 1;
+    uint64_t gen = 0;
     aesrt::BatchReq rq;
     for (;;) {
-        uint32_t d = 0, t = 0, seq = 0, quit = 0;
-        if (lane == 0)
-            quit = !ring_pop(ring, &d, &t, &seq);
-        quit = __shfl_sync(0xffffffffu, quit, 0);
-        if (quit)
+        uint32_t d = 0, t = 0, seq = 0, nt = 0;
+        if (!ring_pop_warp(ring, &d, &t, &seq, &nt))
             break;
-        d = __shfl_sync(0xffffffffu, d, 0);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        seq = __shfl_sync(0xffffffffu, seq, 0);
         if (lane == 0 && t == 0)
             trace(p, seq, kTrFirstPop);
         SrvRec *rec = p.recs + d;
         if (d != cur_d || seq != cur_seq) {  // a new request for this warp: load it and its keys
+            // the request (64 bytes), then seq_ntiles/gen and the tile shape:
+            // one 128-byte line, six independent loads
             const uint4 *src = reinterpret_cast<const uint4 *>(&rec->rq);
             uint4 *dst = reinterpret_cast<uint4 *>(&rq);
+            uint4 w[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                w[i] = __ldcg(src + i);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                dst[i] = __ldcg(src + i);
-            tg = __ldcg(&rec->tile_groups);
-            tp = __ldcg(&rec->tile_parts);
+                dst[i] = w[i];
+            static_assert(offsetof(SrvRec, gen) == 72 && offsetof(SrvRec, tile_groups) == 80 &&
+                              offsetof(SrvRec, tile_parts) == 84,
+                          "record words read as uint4 4 and 5");
+            gen = ((uint64_t)w[4].w << 32) | w[4].z;
+            tg = w[5].x;
+            tp = w[5].y;
             __syncwarp();
 #ifdef SRV_TRACE
             if (lane == 0 && t == 0) {  // a move that reads the record waits for it, then the stamp
@@ -198,18 +198,18 @@ __global__ void __launch_bounds__(512, 1) server_kernel(const __grid_constant__ 
             default: run_part_regs<14, 2>(rq, first, last, part, tp, smem, ln, p, seq, lane == 0 && t == 0); break;
             }
         }
-        // Order this lane's output stores before the tile is counted: at
-        // system scope when the output lives in host memory, else GPU scope
-        // (the completing thread's system-scope release covers the rest).
+        // Order the tile's output stores before it is counted: a warp
+        // barrier gathers every lane's stores under lane 0, whose
+        // acquire-release add publishes them (GPU scope) to the worker that
+        // raises the completion word with a system-scope release.  Outputs
+        // in host memory are fenced at system scope by every lane first.
         if (rq.pad & kFlagHostOut)
             __threadfence_system();
-        else
-            __threadfence();
         __syncwarp();
         if (lane == 0 && t == 0)
             trace(p, seq, kTrFirstTileDone);
         if (lane == 0)
-            tile_finished(p, d);
+            tile_finished(p, d, nt, seq, gen);
     }
 }
 
@@ -244,6 +244,7 @@ struct offload_server_s {
     std::vector<uint64_t> lens;    // per slot, payload length
     std::unique_ptr<std::atomic<uint64_t>[]> live;  // per slot, live ticket (0 = free)
     std::vector<int> key_used;
+    std::vector<uint8_t> key_nr;   // per key slot, Nr of its key (sent with each request)
     std::atomic<uint64_t> next_seq{1};
     std::atomic<uint64_t> inflight{0};
     std::atomic<bool> stopping{false};
@@ -353,7 +354,7 @@ int enqueue(offload_server_s *s, uint32_t key_slot, uint64_t iv_hi, uint64_t iv_
     qe.iv_hi = iv_hi;
     qe.iv_lo = iv_lo;
     qe.gen = gen;
-    qe.key_slot = key_slot;
+    qe.key_slot = key_slot | (uint32_t)s->key_nr[key_slot] << 24;
     qe.desc = (uint16_t)d;
     qe.flags = (uint16_t)flags;
     qe.tag = seq + 1;
@@ -427,6 +428,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     for (int i = 0; i < slots; ++i)
         s->live[i].store(0);
     s->key_used.assign(max_keys, 0);
+    s->key_nr.assign(max_keys, 0);
 
     cudaError_t e = cudaSuccess;
     auto fail = [&](const char *where) {
@@ -457,15 +459,14 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     std::memset(s->done, 0, sizeof(unsigned long long) * slots);
     std::memset(s->ctrl, 0, 64);
     // device: cursor, adv and disp each on a 4 KiB page of their own (every
-    // agent polls them), then disp_ring, recs, keys, key_nr and the key
-    // staging area (registration allocates nothing: cudaFree would wait for
-    // the resident kernel to exit)
+    // agent polls them), then disp_ring, recs, keys and the key staging area
+    // (registration allocates nothing: cudaFree would wait for the resident
+    // kernel to exit)
     const size_t off_adv = 4096, off_disp = 8192, off_slots = 12288;
     const size_t off_recs = 16384;
     static_assert(8 * kDispRing <= 4096, "disp_ring fits in its page");
     const size_t off_keys = off_recs + sizeof(SrvRec) * (size_t)slots;
-    const size_t off_nr = off_keys + 240 * (size_t)max_keys;
-    const size_t off_stage = (off_nr + sizeof(int) * (size_t)max_keys + 255) / 256 * 256;
+    const size_t off_stage = (off_keys + 240 * (size_t)max_keys + 255) / 256 * 256;
     const size_t dbytes = off_stage + 64;
     if ((e = cudaMalloc(&s->dmem, dbytes)))
         return fail("cudaMalloc(server)");
@@ -488,7 +489,6 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     P.disp_ring = reinterpret_cast<unsigned long long *>(s->dmem + off_slots);
     P.recs = reinterpret_cast<SrvRec *>(s->dmem + off_recs);
     P.keys = reinterpret_cast<const uint4 *>(s->dmem + off_keys);
-    P.key_nr = reinterpret_cast<const int *>(s->dmem + off_nr);
     s->key_stage = s->dmem + off_stage;
     if (s->trace_requests) {
         const size_t tb = sizeof(unsigned long long) * kTracePoints * (size_t)s->trace_requests;
@@ -517,6 +517,7 @@ int offload_server_create(offload_server_t *out, const offload_cfg_t *cfg)
     P.max_keys = (uint32_t)max_keys;
     P.tile_blocks = (uint32_t)tile_blocks;
     P.nslots = (uint32_t)slots;
+    P.nctas = (uint32_t)ctas;
     P.idle_ns = s->idle_ns;
     P.max_len = s->max_len;
     if ((e = cudaFuncSetAttribute(server_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -563,12 +564,10 @@ int offload_key_register(offload_server_t s, const uint8_t *key, int bits, int *
     if (!e)
         e = launch_key_expand(stage, reinterpret_cast<const int32_t *>(stage + 32), st->te0, w, 1, s->setup);
     if (!e)
-        e = cudaMemcpyAsync(const_cast<int *>(s->params.key_nr) + slot, &nr, sizeof(int),
-                            cudaMemcpyHostToDevice, s->setup);
-    if (!e)
         e = cudaStreamSynchronize(s->setup);
     if (e)
         return cuda_fail(e, "offload_key_register");
+    s->key_nr[slot] = (uint8_t)nr;
     s->key_used[slot] = 1;
     *slot_out = slot;
     return AES_OK;

@@ -112,12 +112,18 @@ std::vector<BatchShape> batch_candidates()
 // Time every candidate as a graph plan over `reqs` (median of `reps` launches
 // after two warm-ups, CUDA events on `s`); the fastest in *pick.  Returns
 // AES_OK, or the first error if no candidate ran.
-int sweep_batch(const std::vector<aes_desc_t> &reqs, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps,
-                BatchShape *pick, float *best_ms)
+int sweep_batch(DeviceState &st, const std::vector<aes_desc_t> &reqs, cudaStream_t s, cudaEvent_t a,
+                cudaEvent_t b, int reps, BatchShape *pick, float *best_ms)
 {
     float best = 1e30f;
     int err = AES_EINVAL;
+    st.n_batch_results = 0;
     for (const BatchShape &c : batch_candidates()) {
+        const int slot = st.n_batch_results < DeviceState::kMaxBatchCandidates ? st.n_batch_results++ : -1;
+        if (slot >= 0) {
+            st.batch_results[slot] = c;
+            st.batch_results_ms[slot] = -1.f;
+        }
         aes_batch_opts_t o{};
         o.variant = c.variant;
         o.threads = c.threads;
@@ -145,6 +151,8 @@ int sweep_batch(const std::vector<aes_desc_t> &reqs, cudaStream_t s, cudaEvent_t
         if (t.empty())
             continue;
         std::sort(t.begin(), t.end());
+        if (slot >= 0)
+            st.batch_results_ms[slot] = t[t.size() / 2];
         if (t[t.size() / 2] < best) {
             best = t[t.size() / 2];
             *pick = c;
@@ -185,7 +193,7 @@ int tune_batch(DeviceState &st, void *in, void *out, size_t cap, cudaStream_t s,
     }
     BatchShape pick = st.batch_tuned;
     if (!rc)
-        rc = sweep_batch(reqs, s, a, b, 6, &pick, nullptr);
+        rc = sweep_batch(st, reqs, s, a, b, 6, &pick, nullptr);
     aes_ctx_destroy(ctx[0]);
     aes_ctx_destroy(ctx[1]);
     if (!rc)
@@ -318,7 +326,7 @@ int aes_batch_autotune(const aes_desc_t *descs, int n, void *stream, aes_batch_o
         return cuda_fail(e, "aes_batch_autotune events");
     }
     BatchShape pick = st->batch_tuned;
-    rc = sweep_batch(reqs, s, a, b, 5, &pick, nullptr);
+    rc = sweep_batch(*st, reqs, s, a, b, 5, &pick, nullptr);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc)
@@ -333,6 +341,26 @@ int aes_batch_autotune(const aes_desc_t *descs, int n, void *stream, aes_batch_o
         best->blocks_per_thread = pick.nb;
     }
     return AES_OK;
+}
+
+int aes_batch_tune_results(aes_batch_opts_t *shapes, float *ms, int cap)
+{
+    if (cap < 0 || (cap > 0 && (!shapes || !ms)))
+        return AES_EINVAL;
+    DeviceState *st = nullptr;
+    int rc = device_state(&st);
+    if (rc)
+        return rc;
+    const int n = st->n_batch_results < cap ? st->n_batch_results : cap;
+    for (int i = 0; i < n; ++i) {
+        std::memset(&shapes[i], 0, sizeof(shapes[i]));
+        shapes[i].variant = st->batch_results[i].variant;
+        shapes[i].threads = st->batch_results[i].threads;
+        shapes[i].tile_blocks = st->batch_results[i].tile_blocks;
+        shapes[i].blocks_per_thread = st->batch_results[i].nb;
+        ms[i] = st->batch_results_ms[i];
+    }
+    return n;
 }
 
 int aes_batch_tuned_shape(aes_batch_opts_t *out)

@@ -54,9 +54,10 @@ struct Tile {
 
 // One stand-in CTA: the agent and kWorkers worker warps, joined by the
 // kernel's own shared ring (served_protocol.cuh).
-constexpr int kWorkers = 2;
+constexpr int kWorkers = 5;  // warps 1..5: partitions 1, 2, 3, 0, 1
 struct Cta {
     Ring ring{};
+    Cta() { ring_init(ring); }
 };
 
 struct Sim {
@@ -120,7 +121,6 @@ struct Sim {
         P.disp_ring = ring.data();
         P.recs = recs;
         P.keys = keys.data();
-        P.key_nr = key_nr.data();
         P.queue = queue;
         P.order = order.data();
         P.done = done.data();
@@ -131,6 +131,7 @@ struct Sim {
         P.max_keys = kMaxKeys;
         P.tile_blocks = (uint32_t)tile_blocks;
         P.nslots = (uint32_t)slots;
+        P.nctas = (uint32_t)nctas;
         P.idle_ns = idle_ns;
         P.max_len = 1ull << 40;
 #ifdef SRV_TRACE
@@ -200,27 +201,34 @@ struct Sim {
 
     // A worker warp's lane 0: the kernel's ring_pop, the tile (checked here
     // instead of encrypted) and the kernel's completion step.
-    void worker_thread(Cta *c)
+    void worker_thread(Cta *c, uint32_t warp)
     {
         for (;;) {
             Tile tl{};
-            if (!ring_pop(c->ring, &tl.d, &tl.t, &tl.seq))
+            uint32_t nt = 0;
+            if (!ring_pop(c->ring, warp, &tl.d, &tl.t, &tl.seq, &nt))
                 break;
             if (tl.t == 0)
                 trace(P, tl.seq, kTrFirstPop);
-            process(tl);
-            tile_finished(P, tl.d);
+            // the kernel's worker reads the record's generation with the record
+            const uint64_t gen = ld_cg(&recs[tl.d].gen);
+            process(tl, nt);
+            tile_finished(P, tl.d, nt, tl.seq, gen);
         }
         drain_stores();
         live.fetch_sub(1);
     }
 
-    void process(const Tile &tl)
+    void process(const Tile &tl, uint32_t item_nt)
     {
         const uint64_t sn = ld_relaxed_gpu(&recs[tl.d].seq_ntiles);
         const uint32_t nt = (uint32_t)(sn & kTileMask);
         if ((uint32_t)(sn >> kTileBits) != tl.seq || tl.t >= nt) {
             fail("tile %llu of seq %llu: slot holds seq %llu", tl.t, tl.seq, sn >> kTileBits);
+            return;
+        }
+        if (item_nt != nt) {
+            fail("seq %llu: ring item says %llu tiles, record %llu", tl.seq, item_nt, nt);
             return;
         }
         const uint64_t idx = tl.seq - 1;
@@ -254,8 +262,8 @@ struct Sim {
                 threads.emplace_back([this, c] { agent_thread<true>(c); });
             else
                 threads.emplace_back([this, c] { agent_thread<false>(c); });
-            for (int w = 0; w < kWorkers; ++w)
-                threads.emplace_back([this, c] { worker_thread(c); });
+            for (int w = 1; w <= kWorkers; ++w)
+                threads.emplace_back([this, c, w] { worker_thread(c, (uint32_t)w); });
         }
     }
 
@@ -354,7 +362,7 @@ struct Sim {
             qe.iv_hi = 0x0123456789abcdefull;
             qe.iv_lo = r.iv_lo;
             qe.gen = gn;
-            qe.key_slot = (uint32_t)r.key_slot;
+            qe.key_slot = (uint32_t)r.key_slot | (uint32_t)key_nr[(size_t)r.key_slot] << 24;  // slot | Nr
             qe.desc = (uint16_t)d;
             qe.flags = r.emulated ? (uint16_t)kFlagEmulated : 0;
             qe.tag = seq + 1;

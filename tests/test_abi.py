@@ -99,6 +99,8 @@ def test_host_side_argument_errors(lib):
     assert lib.aes_batch_autotune(None, 3, None, None) == A.AES_EINVAL
     assert lib.aes_batch_tuned_shape(None) == A.AES_EINVAL
     assert lib.aes_measure_peaks(None) == A.AES_EINVAL
+    assert lib.aes_batch_tune_results(None, None, 4) == A.AES_EINVAL
+    assert lib.aes_batch_tune_results(None, None, -1) == A.AES_EINVAL
 
 
 def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):

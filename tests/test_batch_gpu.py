@@ -150,14 +150,17 @@ def test_batch_argument_errors(cuda, aes):
     cuda.cuda.synchronize()
 
 
-def test_full_size_batch_workload_sampled(cuda, aes, ncpu):
-    """The 4096-request workload at full size (~3.8 GB), launched as the
-    benchmark launches it (a graph plan with the tuned shape).  Checked: 12
-    whole requests and four 4 KiB windows in 256 others, each against the
-    oracle started at the window's counter."""
+def test_full_size_batch_workload_matches_oracle(cuda, aes, ncpu):
+    """The 4096-request workload at full size (~3.7 GB), launched as the
+    benchmark launches it (a graph plan with the device's batch shape), and
+    every byte of every request compared with the oracle (about 80 s of
+    oracle time on 16 host cores), as is every byte past each request up to
+    the next 256-byte boundary (untouched)."""
+    import concurrent.futures as cf
+
     w = W.batch_varlen(seed=W.SEED_BASE + 3)
     src = to_dev(cuda, w.payload)
-    dst = cuda.empty(w.arena_bytes, dtype=cuda.uint8, device="cuda")
+    dst = cuda.full((w.arena_bytes,), 0xA5, dtype=cuda.uint8, device="cuda")
     ctxs = [aes.Context(w.key_of(i).tobytes(), int(w.bits[i])) for i in range(w.n)]
     reqs = [(ctxs[i], w.ivs[i].tobytes(), src.data_ptr() + int(w.offsets[i]),
              dst.data_ptr() + int(w.offsets[i]), int(w.lengths[i])) for i in range(w.n)]
@@ -165,24 +168,31 @@ def test_full_size_batch_workload_sampled(cuda, aes, ncpu):
     assert plan.nbytes == w.total_bytes
     plan.launch()
     cuda.cuda.synchronize()
-    g = W.rng(53)
-    small = [i for i in range(w.n) if w.lengths[i] <= (256 << 10)]
-    whole = list(g.choice(small, 8, replace=False)) + [int(np.argmax(w.lengths))] + \
-        [i for i in range(w.n) if w.lengths[i] % 16][:3]
-    for i in whole:
-        o, n = int(w.offsets[i]), int(w.lengths[i])
-        want = oracle.ctr_mt(w.key_of(i), int(w.bits[i]), w.ivs[i], w.payload[o: o + n], ncpu)
-        np.testing.assert_array_equal(to_host(dst[o: o + n]), want, err_msg=f"request {i}")
-    for i in g.choice(w.n, 256, replace=False):
-        o, n = int(w.offsets[i]), int(w.lengths[i])
-        for _ in range(4):
-            start = int(g.integers(0, max(1, n // 16))) * 16
-            end = min(n, start + 4096)
-            want = oracle.ctr(w.key_of(i), int(w.bits[i]), iv_plus(w.ivs[i], start // 16),
-                              w.payload[o + start: o + end])
-            np.testing.assert_array_equal(to_host(dst[o + start: o + end]), want,
-                                          err_msg=f"request {i} window {start}")
     plan.close()
+    out = to_host(dst)
+    del src, dst
+
+    def check(i):
+        o, n = int(w.offsets[i]), int(w.lengths[i])
+        want = oracle.ctr_mt(w.key_of(i), int(w.bits[i]), w.ivs[i], w.payload[o: o + n],
+                             ncpu if n >= (8 << 20) // 4 else 1)
+        if not np.array_equal(out[o: o + n], want):
+            bad = int(np.flatnonzero(out[o: o + n] != want)[0])
+            return f"request {i} (len {n}) differs from byte {bad}"
+        pad_end = (o + n + 255) // 256 * 256
+        if not (out[o + n: pad_end] == 0xA5).all():
+            return f"request {i}: bytes past len were written"
+        return None
+
+    # large requests use every core each; the many small ones run side by side
+    order = sorted(range(w.n), key=lambda i: -int(w.lengths[i]))
+    big = [i for i in order if w.lengths[i] >= (8 << 20) // 4]
+    small = [i for i in order if w.lengths[i] < (8 << 20) // 4]
+    errors = [e for e in map(check, big) if e]
+    with cf.ThreadPoolExecutor(ncpu) as ex:
+        errors += [e for e in ex.map(check, small) if e]
+    assert not errors, errors[:5]
+    cuda.cuda.empty_cache()
 
 
 def test_batch_pinned_host_buffers(cuda, aes, ncpu):

@@ -93,3 +93,44 @@ def test_clock_summary(bench):
 def test_workload_name(bench):
     assert bench.workload_name(4096) == bench.WORKLOAD
     assert bench.workload_name(512).startswith("512 requests of: ")
+
+
+class _FakeProps:
+    multi_processor_count = 152
+
+
+class _FakeCuda:
+    @staticmethod
+    def get_device_properties(dev):
+        return _FakeProps()
+
+
+class _FakeTorch:
+    cuda = _FakeCuda()
+
+
+def test_bitslice_ops_counts_the_circuit(bench):
+    """Per 32 blocks: 16 S-box circuits of 113 gates per round, 416
+    MixColumns xors per full round, 128 key xors per round key."""
+    class One:
+        lengths = np.array([32 * 16, 32 * 16])
+        bits = np.array([128, 256])
+    want = (16 * 113 * 10 + 416 * 9 + 128 * 11) + (16 * 113 * 14 + 416 * 13 + 128 * 15)
+    assert bench.bitslice_ops(One) == pytest.approx(want)
+
+
+def test_batch_roofline_divides_by_the_measured_rate_of_the_picked_variant(bench):
+    w = W.batch_varlen(n=16, min_len=1024, max_len=1 << 20, seed=12, with_payload=False)
+    rates = {"lds32_per_clk_sm": 16.0, "lop3_per_clk_sm": 32.0, "zero_copy_each_way_gbs": 100.0}
+    step = int(w.lengths.sum())
+    tt = bench.batch_roofline(_FakeTorch, 0, w, step, [1e-3], {"variant": 1}, rates)
+    bs = bench.batch_roofline(_FakeTorch, 0, w, step, [1e-3], {"variant": 2}, rates)
+    f = float(bench.peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6
+    assert tt["kernel"] == "batch_ttable_kernel" and bs["kernel"] == "batch_bitslice_kernel"
+    assert tt["peak"] == pytest.approx(step / (bench.ttable_lookups(w) / (16.0 * 152 * f)) / 1e9, rel=1e-3)
+    assert bs["peak"] == pytest.approx(step / (bench.bitslice_ops(w) / (32.0 * 152 * f)) / 1e9, rel=1e-3)
+    assert tt["achieved"] == pytest.approx(step / 1e-3 / 1e9, abs=0.01)  # rounded to 2 decimals
+    assert "measured on this GPU" in tt["peak_basis"]
+    nominal = bench.batch_roofline(_FakeTorch, 0, w, step, [1e-3], {"variant": 1}, {"error": "no GPU"})
+    assert "nominal rate" in nominal["peak_basis"]
+    assert nominal["peak"] == pytest.approx(2 * tt["peak"], rel=1e-3)  # 32 per clk instead of the fake 16

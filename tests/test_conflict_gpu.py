@@ -77,3 +77,32 @@ def test_more_handlers_than_server_slots(cuda, aes):
         assert r["lost_updates"] == 0 and r["final_count"] == 1000, r
     finally:
         assert srv.close() == aes.AES_OK
+
+
+# ---- the detector's host-only parts, on the host the GPU is attached to ----
+# The store emulation decodes the faulting store instruction, so it depends
+# on the CPU architecture: x86-64 where the CPU tests run, AArch64 (Grace) on
+# GB300 machines.  These re-run the CPU suite's store-emulation checks there.
+
+def test_store_emulation_selftest_on_the_gpu_host(aes):
+    import platform
+
+    import test_conflict_cpu as cpu
+
+    r = aes.store_selftest(6000)
+    print(f"store self-test on {platform.machine()}: {r}")
+    cpu.test_store_emulation_selftest()
+
+
+@pytest.mark.parametrize("mode", [A.CDET_DETECT, A.CDET_ENFORCE], ids=["detect", "enforce"])
+def test_emulated_stores_on_the_gpu_host(aes, mode):
+    import test_conflict_cpu as cpu
+
+    cpu.test_emulated_stores_keep_the_detectors_results(mode)
+    cpu.test_protection_changes_per_guarded_write()
+
+
+def test_detector_under_ubsan_on_the_gpu_host(aes, tmp_path):
+    import test_conflict_cpu as cpu
+
+    cpu.test_detector_under_undefined_behaviour_sanitizer(tmp_path, "-O2")

@@ -573,6 +573,53 @@ def test_full_size_8mib_aes256_stream_sampled(cuda, aes, ncpu, budget_gib):
     cuda.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("rate", [100_000.0, None], ids=["poisson_100k", "all_at_once"])
+def test_served_open_loop_mix_matches_oracle(cuda, aes, ncpu, rate):
+    """The served open-loop workload as the served study offers it -- sizes
+    70% 1 MiB, 10% 8 MiB (uncapped), 20% log-uniform 4-64 KiB; 64 registered
+    keys, AES-128/256 50/50, one drawn per request; 8 native submitter
+    threads, Poisson arrivals or everything at once -- and every byte of every
+    request compared with the oracle."""
+    import concurrent.futures as cf
+
+    n = 384
+    sizes = W.served_sizes(n, seed=W.SEED_BASE + 4)
+    kbits, kbytes = W.key_set(64, seed=W.SEED_BASE + 5)
+    g = W.rng(W.SEED_BASE + 6)
+    key_idx = g.integers(0, 64, n)
+    ivs = W.random_bytes(g, 16 * n).reshape(n, 16)
+    payload, offs, src, dst = arena(cuda, g, [int(x) for x in sizes])
+    srv = aes.Server(slots=1024, max_keys=64, idle_timeout_us=2_000_000)
+    try:
+        slots = np.array([srv.key_register(kbytes[i, : kbits[i] // 8].tobytes(), int(kbits[i])) for i in range(64)])
+        reqs = np.zeros(n, dtype=aes.drive_dtype())
+        reqs["key_slot"] = slots[key_idx]
+        reqs["iv"] = ivs
+        reqs["inp"] = src.data_ptr() + offs
+        reqs["out"] = dst.data_ptr() + offs
+        reqs["len"] = sizes
+        reqs["arrival_s"] = 0.0 if rate is None else W.poisson_arrivals(n, rate, seed=W.SEED_BASE + 44)
+        lat, res = aes.drive_served(srv, reqs, 8)
+        assert res["errors"] == 0 and res["bytes"] == int(sizes.sum()) and (lat > 0).all()
+    finally:
+        assert srv.close() == aes.AES_OK
+    out = to_host(dst)
+
+    def check(i):
+        k = int(key_idx[i])
+        o, m = int(offs[i]), int(sizes[i])
+        want = oracle.ctr_mt(kbytes[k, : kbits[k] // 8], int(kbits[k]), ivs[i], payload[o: o + m], 2)
+        if not np.array_equal(out[o: o + m], want):
+            return f"request {i} (len {m}) differs"
+        if not (out[o + m: o + m + 16] == 0xA5).all():
+            return f"request {i}: bytes past len were written"
+        return None
+
+    with cf.ThreadPoolExecutor(max(1, ncpu // 2)) as ex:
+        errors = [e for e in ex.map(check, range(n)) if e]
+    assert not errors, errors[:5]
+
+
 @pytest.mark.parametrize("cfg", [dict(threads=64, ctas=2, tile_blocks=64), dict(threads=96, ctas=1, tile_blocks=128),
                                  dict(threads=512, tile_blocks=256), dict()])
 def test_server_shapes_match_oracle(cuda, aes, ncpu, cfg):
