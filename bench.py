@@ -1021,8 +1021,28 @@ def run_extras(A, torch, dev, stream, sh, w, ctxs, reqs, src, dst, step_bytes, a
     b.record(stream)
     stream.synchronize()
     one_shot = step_bytes * reps / (a.elapsed_time(b) / 1e3) / 1e9
+    # aes_ctr_batch_noalloc over the same requests, in calls of at most 1024
+    # (its cap; calls on one stream run one after another, so they may share
+    # its static descriptor array)
+    def noalloc_step():
+        for i in range(0, len(reqs), 1024):
+            rc = A.batch_noalloc_status(reqs[i: i + 1024], stream=sh)
+            if rc != A.AES_OK:
+                raise A.AesError(rc, "aes_ctr_batch_noalloc")
+
+    noalloc_step()
+    stream.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        noalloc_step()
+    b.record(stream)
+    stream.synchronize()
+    na = step_bytes * reps / (a.elapsed_time(b) / 1e3) / 1e9
     out["per_call"] = {"value": round(pc, 3), "unit": UNIT, "launches_per_step": len(reqs),
                        "how": "4096 aes_ctr calls on one stream, tuned shapes"}
+    out["batch_noalloc"] = {"value": round(na, 3), "unit": UNIT, "calls_per_step": -(-len(reqs) // 1024),
+                            "how": "aes_ctr_batch_noalloc in calls of 1024 requests (descriptor copy + launch "
+                                   "each call, no device allocation)"}
     out["batch_one_shot"] = {"value": round(one_shot, 3), "unit": UNIT,
                              "how": "aes_ctr_batch (descriptor upload + launch each call)"}
 
