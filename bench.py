@@ -669,7 +669,7 @@ def conflict_study(args, rank, local):
             # per-handler buffers at `stride` apart: pass views so the stride matches
             def run(mode, n):
                 return A.conflict_run(mode, handlers, n, 64, server=srv, key_slot=ks, buf_in=src, buf_out=dst,
-                                      nbytes=nbytes)
+                                      nbytes=nbytes, emulate_stores=False)
             run(A.CDET_UNPROTECTED, 500)  # warm-up
             rows = {}
             for mode, name in names.items():
@@ -693,11 +693,11 @@ def conflict_study(args, rank, local):
         taxonomy = {}
         for pat, name in pats.items():
             r = A.conflict_run(A.CDET_DETECT, handlers, requests, 64, server=srv, key_slot=ks, buf_in=src,
-                               buf_out=dst, nbytes=min(sizes), pattern=pat)
+                               buf_out=dst, nbytes=min(sizes), pattern=pat, emulate_stores=False)
             taxonomy[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
         n1 = 5000
         off = A.conflict_run(A.CDET_UNPROTECTED, 1, n1, 1, offload_ns=0)
-        on = A.conflict_run(A.CDET_DETECT, 1, n1, 1, offload_ns=0)
+        on = A.conflict_run(A.CDET_DETECT, 1, n1, 1, offload_ns=0, emulate_stores=False)
         fault_us = (on["elapsed_s"] - off["elapsed_s"]) / n1 * 1e6
         on_e = A.conflict_run(A.CDET_DETECT, 1, n1, 1, offload_ns=0, emulate_stores=True)
         fault_emu_us = (on_e["elapsed_s"] - off["elapsed_s"]) / n1 * 1e6

@@ -498,6 +498,10 @@ int aes_ctr_drive(const aes_ctx_t *ctxs, int nctx, const aes_drive_req_t *reqs, 
                                      needs counters >= handlers */
 #define CDET_PATTERN_LOCKED 3     /* the application holds a lock across its read-modify-write */
 
+/* cdet_run_cfg_t.store_mode */
+#define CDET_STORES_EMULATE 0     /* the fault handler performs guarded stores (default) */
+#define CDET_STORES_UNPROTECT 1   /* guarded writes unprotect the page */
+
 typedef struct {
     int handlers;
     int requests;
@@ -511,13 +515,21 @@ typedef struct {
     void *buf_out;
     size_t bytes;
     int pattern;            /* CDET_PATTERN_*; 0 = the shared unlocked counter */
-    int emulate_stores;     /* detector: keep the pages read-only and perform each
-                               faulting store in the fault handler (through a
-                               second, writable mapping), so a guarded write
-                               changes no protection; stores it cannot decode
-                               (only plain general-register stores are: x86-64
-                               MOV, AArch64 STR/STUR) unprotect the page as
-                               when this is 0 */
+    int store_mode;         /* detector, how a guarded write proceeds:
+                               CDET_STORES_EMULATE (0, the default): the pages
+                               stay read-only and the fault handler performs
+                               each faulting store itself (through a second,
+                               writable mapping), so a guarded write changes no
+                               protection (0.8 us a write on the Grace host);
+                               stores it cannot decode (only plain
+                               general-register stores are: x86-64 MOV, AArch64
+                               STR/STUR/STTR) unprotect the page instead.
+                               CDET_STORES_UNPROTECT: unprotect the page at the
+                               write and protect it again when the writer parks
+                               or finishes (two protection changes, 48 us a write
+                               in a process with a CUDA context on the Grace
+                               host, where the GPU shares the page tables).
+                               Other values: AES_EINVAL. */
 } cdet_run_cfg_t;
 
 typedef struct {

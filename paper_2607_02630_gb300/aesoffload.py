@@ -88,7 +88,7 @@ class CdetCfg(ctypes.Structure):
                 ("counters_per_page", ctypes.c_int), ("mode", ctypes.c_int), ("offload_ns", ctypes.c_uint64),
                 ("srv", ctypes.c_void_p), ("key_slot", ctypes.c_int), ("buf_in", ctypes.c_void_p),
                 ("buf_out", ctypes.c_void_p), ("bytes", ctypes.c_size_t), ("pattern", ctypes.c_int),
-                ("emulate_stores", ctypes.c_int)]
+                ("store_mode", ctypes.c_int)]
 
 
 class CdetResult(ctypes.Structure):
@@ -99,6 +99,7 @@ class CdetResult(ctypes.Structure):
 
 CDET_UNPROTECTED, CDET_LOCK, CDET_DETECT, CDET_ENFORCE = 0, 1, 2, 3
 CDET_PATTERN_SHARED, CDET_PATTERN_READONLY, CDET_PATTERN_PER_CONN, CDET_PATTERN_LOCKED = 0, 1, 2, 3
+CDET_STORES_EMULATE, CDET_STORES_UNPROTECT = 0, 1
 
 
 class DriveOpts(ctypes.Structure):
@@ -550,14 +551,16 @@ def drive_per_call(ctxs, reqs, nthreads: int = 8):
 
 def conflict_run(mode: int, handlers: int = 16, requests: int = 4000, counters: int = 64, counters_per_page: int = 1,
                  offload_ns: int = 50_000, server: "Server | None" = None, key_slot: int = 0, buf_in=0, buf_out=0,
-                 nbytes: int = 0, pattern: int = 0, emulate_stores: bool = False) -> dict:
+                 nbytes: int = 0, pattern: int = 0, emulate_stores: bool = True) -> dict:
     """cdet_run: the conflict detector's synthetic server (read a shared
     counter, park at an offload, write it back incremented) in one of the
     CDET_* modes, with the shared state in one of the CDET_PATTERN_*
-    patterns; returns the result as a dict (requests/s added)."""
+    patterns; returns the result as a dict (requests/s added).
+    emulate_stores: CDET_STORES_EMULATE (the default) or, if False,
+    CDET_STORES_UNPROTECT."""
     cfg = CdetCfg(int(handlers), int(requests), int(counters), int(counters_per_page), int(mode), int(offload_ns),
                   server.handle if server else None, int(key_slot), ptr(buf_in) or None, ptr(buf_out) or None,
-                  int(nbytes), int(pattern), int(bool(emulate_stores)))
+                  int(nbytes), int(pattern), CDET_STORES_EMULATE if emulate_stores else CDET_STORES_UNPROTECT)
     res = CdetResult()
     _check(lib().cdet_run(ctypes.byref(cfg), ctypes.byref(res)), "cdet_run")
     out = {f: getattr(res, f) for f, _ in CdetResult._fields_}

@@ -42,7 +42,8 @@
 // taken on the handler's own stack; it suits handlers whose writes before
 // the conflicting one may be repeated (true of the workload here).
 //
-// With cfg.emulate_stores the pages are never unprotected: the fault
+// With cfg.store_mode == CDET_STORES_EMULATE (the default) the pages are
+// never unprotected: the fault
 // handler performs the store itself through a writable alias of the region
 // (see "store emulation" below), so every write faults and a page also
 // records which handler stamped it (a handler's own later writes are no
@@ -128,7 +129,7 @@ void protect_dirty(Run &r, Fiber &f)
     f.dirty_hi = -1;
 }
 
-// ---- store emulation (cfg.emulate_stores) --------------------------------
+// ---- store emulation (cfg.store_mode == CDET_STORES_EMULATE) -------------
 // The shared pages stay read-only for the whole run.  The fault handler
 // performs the faulting store itself, through a second, writable mapping
 // of the same memory, and steps the program counter past it.  A guarded
@@ -464,6 +465,7 @@ int cdet_run(const cdet_run_cfg_t *cfg, cdet_run_result_t *res)
         cfg->counters_per_page < 1 || cfg->counters_per_page > 64 || cfg->mode < CDET_UNPROTECTED ||
         cfg->mode > CDET_ENFORCE || (cfg->bytes && (!cfg->srv || !cfg->buf_in || !cfg->buf_out)) ||
         cfg->pattern < CDET_PATTERN_SHARED || cfg->pattern > CDET_PATTERN_LOCKED ||
+        (cfg->store_mode != CDET_STORES_EMULATE && cfg->store_mode != CDET_STORES_UNPROTECT) ||
         (cfg->pattern == CDET_PATTERN_PER_CONN && cfg->counters < cfg->handlers))
         return AES_EINVAL;
     if (g_run)
@@ -475,7 +477,7 @@ int cdet_run(const cdet_run_cfg_t *cfg, cdet_run_result_t *res)
     r.region_bytes = (size_t)r.npages * (size_t)r.page;
     r.detector = cfg->mode == CDET_DETECT || cfg->mode == CDET_ENFORCE;
     void *m = MAP_FAILED;
-    if (r.detector && cfg->emulate_stores) {
+    if (r.detector && cfg->store_mode == CDET_STORES_EMULATE) {
         // one memory object mapped twice: the handlers' view (read-only
         // while guarded) and the detector's writable alias
         const int fd = memfd_create("cdet_region", MFD_CLOEXEC);

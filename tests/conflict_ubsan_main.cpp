@@ -30,7 +30,7 @@ int main()
                 c.mode = mode;
                 c.offload_ns = 20000;
                 c.pattern = pat;
-                c.emulate_stores = emu;
+                c.store_mode = emu ? CDET_STORES_EMULATE : CDET_STORES_UNPROTECT;
                 cdet_run_result_t r{};
                 const int rc = cdet_run(&c, &r);
                 const bool lost_ok = mode == CDET_UNPROTECTED || mode == CDET_DETECT ? true : r.lost_updates == 0;

@@ -3,6 +3,8 @@ read a shared counter, park at an offload, write it back incremented), with a
 host-timed offload, on the CPU (Sec. 5: unlocked shared aggregates lose
 updates under overlap; the detector flags the conflicts and, enforcing,
 re-runs conflicting handlers serialized)."""
+import ctypes
+
 import pytest
 
 from paper_2607_02630_gb300 import aesoffload as A
@@ -17,8 +19,12 @@ def built():
     build.build()
 
 
-def run(mode, counters=64, handlers=16, offload_ns=50_000, requests=N):
-    return A.conflict_run(mode, handlers=handlers, requests=requests, counters=counters, offload_ns=offload_ns)
+def run(mode, counters=64, handlers=16, offload_ns=50_000, requests=N, emulate=True):
+    return A.conflict_run(mode, handlers=handlers, requests=requests, counters=counters, offload_ns=offload_ns,
+                          emulate_stores=emulate)
+
+
+EMULATE = pytest.mark.parametrize("emulate", [True, False], ids=["emulated_stores", "unprotect"])
 
 
 def test_unprotected_overlap_loses_updates():
@@ -33,24 +39,27 @@ def test_coarse_lock_loses_nothing():
     assert r["lost_updates"] == 0 and r["final_count"] == N
 
 
-def test_detect_flags_every_lost_update():
-    r = run(A.CDET_DETECT)
+@EMULATE
+def test_detect_flags_every_lost_update(emulate):
+    r = run(A.CDET_DETECT, emulate=emulate)
     assert r["lost_updates"] > 0
     assert r["conflicts"] >= r["lost_updates"]
     assert r["restarts"] == 0
 
 
-def test_enforce_loses_nothing():
-    enf = run(A.CDET_ENFORCE)
+@EMULATE
+def test_enforce_loses_nothing(emulate):
+    enf = run(A.CDET_ENFORCE, emulate=emulate)
     assert enf["lost_updates"] == 0 and enf["final_count"] == N
     assert enf["conflicts"] > 0 and enf["restarts"] == enf["conflicts"]
 
 
-def test_enforce_beats_the_coarse_lock():
+@EMULATE
+def test_enforce_beats_the_coarse_lock(emulate):
     """The lock serializes every offload; enforcement serializes only the
     conflicting handlers (200 us offloads, so the detector's own fault costs,
     a few us each, stay small beside them)."""
-    enf = run(A.CDET_ENFORCE, offload_ns=200_000, requests=1000)
+    enf = run(A.CDET_ENFORCE, offload_ns=200_000, requests=1000, emulate=emulate)
     lock = run(A.CDET_LOCK, offload_ns=200_000, requests=1000)
     assert enf["lost_updates"] == 0
     assert enf["req_per_s"] > 1.5 * lock["req_per_s"]
@@ -61,11 +70,13 @@ def test_single_handler_never_conflicts():
     assert r["lost_updates"] == 0 and r["conflicts"] == 0
 
 
-def test_false_sharing_is_conservative():
+@EMULATE
+def test_false_sharing_is_conservative(emulate):
     """Counters sharing a page conflict at page granularity: more conflicts
     than with one counter per page, still no lost update when enforcing."""
-    per_page = A.conflict_run(A.CDET_ENFORCE, handlers=16, requests=N, counters=64, counters_per_page=64)
-    own_page = run(A.CDET_ENFORCE)
+    per_page = A.conflict_run(A.CDET_ENFORCE, handlers=16, requests=N, counters=64, counters_per_page=64,
+                              emulate_stores=emulate)
+    own_page = run(A.CDET_ENFORCE, emulate=emulate)
     assert per_page["lost_updates"] == 0
     assert per_page["conflicts"] > own_page["conflicts"]
 
@@ -77,18 +88,22 @@ def test_bad_arguments():
         A.conflict_run(7)
     with pytest.raises(A.AesError):
         A.conflict_run(A.CDET_LOCK, counters_per_page=65)
+    cfg = A.CdetCfg(16, 10, 64, 1, A.CDET_DETECT, 1000, None, 0, None, None, 0, 0, 2)  # no such store mode
+    assert A.lib().cdet_run(ctypes.byref(cfg), ctypes.byref(A.CdetResult())) == A.AES_EINVAL
 
 
+@EMULATE
 @pytest.mark.parametrize("pattern", [A.CDET_PATTERN_READONLY, A.CDET_PATTERN_PER_CONN, A.CDET_PATTERN_LOCKED],
                          ids=["read_only", "per_connection", "lock_protected"])
-def test_safe_patterns_raise_no_conflict(pattern):
+def test_safe_patterns_raise_no_conflict(pattern, emulate):
     """The three shared-state patterns the paper finds safe under overlap
     (read-only, per-connection, lock-protected) lose nothing and make the
     detector report nothing; the hazardous one, on the same settings, does
     both."""
-    r = A.conflict_run(A.CDET_DETECT, handlers=16, requests=2000, counters=64, pattern=pattern)
+    r = A.conflict_run(A.CDET_DETECT, handlers=16, requests=2000, counters=64, pattern=pattern,
+                       emulate_stores=emulate)
     assert r["conflicts"] == 0 and r["lost_updates"] == 0 and r["final_count"] == 2000, r
-    hazard = A.conflict_run(A.CDET_DETECT, handlers=16, requests=2000, counters=64)
+    hazard = A.conflict_run(A.CDET_DETECT, handlers=16, requests=2000, counters=64, emulate_stores=emulate)
     assert hazard["conflicts"] > 0 and hazard["lost_updates"] > 0
 
 
@@ -141,7 +156,7 @@ def test_protection_changes_per_guarded_write():
     protection changes (unprotect at the fault, protect again after the
     request), and none with store emulation."""
     n = 2000
-    plain = A.conflict_run(A.CDET_DETECT, 1, n, 1, offload_ns=0)
+    plain = A.conflict_run(A.CDET_DETECT, 1, n, 1, offload_ns=0, emulate_stores=False)
     emu = A.conflict_run(A.CDET_DETECT, 1, n, 1, offload_ns=0, emulate_stores=True)
     assert plain["final_count"] == n and emu["final_count"] == n
     assert plain["protect_calls"] == 2 * n and plain["emulated_stores"] == 0

@@ -10,20 +10,25 @@ from paper_2607_02630_gb300 import aesoffload as A
 pytestmark = pytest.mark.gpu
 
 
-def test_enforce_with_served_emulated_offload(cuda, aes):
+EMULATE = pytest.mark.parametrize("emulate", [True, False], ids=["emulated_stores", "unprotect"])
+
+
+@EMULATE
+def test_enforce_with_served_emulated_offload(cuda, aes, emulate):
     srv = aes.Server(slots=64, max_keys=1, ctas=16, idle_timeout_us=500_000)
     try:
         un = aes.conflict_run(aes.CDET_UNPROTECTED, handlers=16, requests=2000, counters=16, offload_ns=20_000,
                               server=srv)
         enf = aes.conflict_run(aes.CDET_ENFORCE, handlers=16, requests=2000, counters=16, offload_ns=20_000,
-                               server=srv)
+                               server=srv, emulate_stores=emulate)
         assert un["lost_updates"] > 0
         assert enf["lost_updates"] == 0 and enf["final_count"] == 2000 and enf["conflicts"] > 0
     finally:
         assert srv.close() == aes.AES_OK
 
 
-def test_enforce_with_real_aes_offload(cuda, aes, ncpu):
+@EMULATE
+def test_enforce_with_real_aes_offload(cuda, aes, ncpu, emulate):
     srv = aes.Server(slots=64, max_keys=1, ctas=32, idle_timeout_us=500_000)
     try:
         key = bytes(range(16))
@@ -33,7 +38,7 @@ def test_enforce_with_real_aes_offload(cuda, aes, ncpu):
         dst = cuda.zeros_like(src)
         cuda.cuda.synchronize()  # the served kernel runs on its own stream
         r = aes.conflict_run(aes.CDET_ENFORCE, handlers=handlers, requests=800, counters=8, server=srv,
-                             key_slot=ks, buf_in=src, buf_out=dst, nbytes=nbytes)
+                             key_slot=ks, buf_in=src, buf_out=dst, nbytes=nbytes, emulate_stores=emulate)
         assert r["lost_updates"] == 0 and r["final_count"] == 800
         # Request q encrypts under IV q (little-endian in bytes 0..3): find the
         # request whose keystream handler 0's block carries, then check the
