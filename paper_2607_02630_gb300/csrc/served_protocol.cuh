@@ -1214,22 +1214,32 @@ SRV_INLINE uint32_t ring_owner_partition(Ring &ring, uint32_t pos)
 // fields (empty items where a waiting worker's partition already runs a tile
 // of this lease and a later waiting worker's is free; `used` holds the
 // lease's partitions), one CTA fence, the new tail, then each filled slot's
-// barrier.  Returns the number of tiles queued.
+// barrier.  Returns the number of tiles queued.  The partitions of the
+// workers waiting in the positions to fill are read once, all at a time,
+// into 4-bit fields of one word, since the placement looks at each several
+// times.
 SRV_INLINE uint32_t push_lease(Ring &ring, uint32_t room, uint32_t d, uint32_t seq, uint32_t lt, uint32_t lend,
                                uint32_t nt, uint32_t &used)
 {
+    static_assert(2 * kMaxClaim * 4 <= 32 && kPartitions < 16, "one 4-bit partition field per position");
     const uint32_t tail = ld_vol(&ring.tail);
     const uint32_t head = ld_vol(reinterpret_cast<volatile unsigned int *>(&ring.head));
+    const int32_t waiting = (int32_t)(head - tail);  // workers wait at tail .. head - 1
+    uint32_t nw = waiting <= 0 ? 0u : (uint32_t)waiting < room ? (uint32_t)waiting : room;
+    nw = nw < 2 * kMaxClaim ? nw : 2 * kMaxClaim;  // ring_room never offers more
+    uint32_t parts = 0;
+    for (uint32_t i = 0; i < nw; ++i)
+        parts |= ring_owner_partition(ring, tail + i) << (4 * i);
     uint32_t filled = 0, tiles = 0;
     while (filled < room && lt + tiles < lend) {
         const uint32_t pos = tail + filled;
         const uint32_t slot = pos % kRing;
         bool skip = false;
-        if ((int32_t)(head - pos) > 0) {  // a worker waits at pos
-            const uint32_t part = ring_owner_partition(ring, pos);
+        if (filled < nw) {  // a worker waits at pos
+            const uint32_t part = (parts >> (4 * filled)) & 15u;
             if (part < kPartitions && ((used >> part) & 1u)) {
-                for (uint32_t q = pos + 1; (int32_t)(head - q) > 0 && q < tail + room; ++q) {
-                    const uint32_t pq = ring_owner_partition(ring, q);
+                for (uint32_t q = filled + 1; q < nw; ++q) {
+                    const uint32_t pq = (parts >> (4 * q)) & 15u;
                     if (pq < kPartitions && !((used >> pq) & 1u)) {
                         skip = true;
                         break;
