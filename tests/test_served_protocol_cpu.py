@@ -154,3 +154,19 @@ def test_randomised_configurations(sim_trace, mode, seed):
     r = subprocess.run([sim_trace, str(mode)] + [str(x) for x in soak_case(seed)], capture_output=True, text=True,
                        timeout=240)
     assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
+
+
+def test_ring_placement_spreads_a_lease_over_partitions(tmp_path):
+    """The agent's tile placement in its CTA ring (push_lease), on fixed
+    cases: tiles of one lease go to workers on distinct SM partitions where a
+    later waiting worker allows it, empty items stand in the skipped
+    positions, unknown owners and room limits are respected, positions wrap
+    around the ring."""
+    nvcc = B._nvcc()
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+    exe = str(tmp_path / "ring_placement_test")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-Wall", "-Wno-unknown-pragmas", "-fsanitize=undefined",
+                    "-fno-sanitize-recover=undefined", "-I", B.INCLUDE, "-I", B.CSRC, "-I", cuda_inc,
+                    os.path.join(HERE, "ring_placement_test.cpp"), "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
