@@ -239,11 +239,18 @@ def stream_handle(s) -> int:
     return int(s.cuda_stream)
 
 
-def _bytes16(iv) -> ctypes.Array:
-    b = bytes(bytearray(iv if isinstance(iv, (bytes, bytearray)) else bytes(memoryview(iv).tobytes())))
+def _iv_bytes(iv) -> bytes:
+    """The 16-byte initial counter block as bytes.  Passed by pointer: the
+    library copies it before the call returns, so no ctypes copy is made."""
+    b = iv if type(iv) is bytes else bytes(iv) if isinstance(iv, bytearray) else memoryview(iv).tobytes()
     if len(b) != 16:
         raise ValueError("iv must be 16 bytes")
-    return (ctypes.c_uint8 * 16).from_buffer_copy(b)
+    return b
+
+
+def _bytes16(iv) -> ctypes.Array:
+    """The initial counter block as a uint8[16] (descriptor fields)."""
+    return (ctypes.c_uint8 * 16).from_buffer_copy(_iv_bytes(iv))
 
 
 def _keybuf(key, bits: int) -> bytes:
@@ -286,9 +293,12 @@ class Context:
 def ctr_status(ctx: Context, iv, src, dst, nbytes: int, stream=None, variant: int = 0,
                threads: int = 0, blocks_per_thread: int = 0, ctas: int = 0) -> int:
     """aes_ctr_ex returning the raw status code."""
+    h = ctx.handle if ctx else None
+    if not (variant or threads or blocks_per_thread or ctas):  # the tuned shape: no options struct
+        return lib().aes_ctr(h, _iv_bytes(iv), ptr(src), ptr(dst), int(nbytes), stream_handle(stream))
     shape = LaunchShape(variant, threads, blocks_per_thread, ctas)
-    return lib().aes_ctr_ex(ctx.handle if ctx else None, _bytes16(iv), ptr(src), ptr(dst),
-                            int(nbytes), stream_handle(stream), ctypes.byref(shape))
+    return lib().aes_ctr_ex(h, _iv_bytes(iv), ptr(src), ptr(dst), int(nbytes), stream_handle(stream),
+                            ctypes.byref(shape))
 
 
 def ctr(ctx: Context, iv, src, dst, nbytes: int | None = None, stream=None, **shape) -> None:
@@ -301,7 +311,7 @@ def ctr(ctx: Context, iv, src, dst, nbytes: int | None = None, stream=None, **sh
 def ctr_sync(ctx: Context, iv, src, dst, nbytes: int, stream=None) -> None:
     """The blocking offload call: aes_ctr, then poll its completion event
     (aes_ctr_sync; the GIL is released for the whole call)."""
-    _check(lib().aes_ctr_sync(ctx.handle, _bytes16(iv), ptr(src), ptr(dst), int(nbytes), stream_handle(stream)),
+    _check(lib().aes_ctr_sync(ctx.handle, _iv_bytes(iv), ptr(src), ptr(dst), int(nbytes), stream_handle(stream)),
            "aes_ctr_sync")
 
 
@@ -438,7 +448,7 @@ class Server:
 
     def submit_status(self, key_slot: int, iv, src, dst, nbytes: int):
         t = ctypes.c_uint64(0)
-        rc = lib().offload_submit(self.handle, int(key_slot), _bytes16(iv), ptr(src), ptr(dst),
+        rc = lib().offload_submit(self.handle, int(key_slot), _iv_bytes(iv), ptr(src), ptr(dst),
                                   int(nbytes), ctypes.byref(t))
         return rc, t.value
 
