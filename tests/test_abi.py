@@ -179,3 +179,20 @@ def test_trace_build_builds_and_exports_its_reader():
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
     exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
     assert "offload_server_trace" in exported and "offload_submit" in exported
+
+
+def test_iv_marshalling():
+    """The initial counter block reaches the library as 16 bytes, from bytes,
+    bytearray or a uint8 array, by pointer for the calls and as a uint8[16]
+    for descriptors; any other length is refused before the call."""
+    import numpy as np
+
+    from paper_2607_02630_gb300 import aesoffload as A
+
+    want = bytes(range(16))
+    for iv in (want, bytearray(want), np.arange(16, dtype=np.uint8)):
+        assert A._iv_bytes(iv) == want
+        assert bytes(A._bytes16(iv)) == want
+    for bad in (b"", bytes(15), bytes(17), np.zeros(8, dtype=np.uint16)[:7]):
+        with pytest.raises(ValueError):
+            A._iv_bytes(bad)
