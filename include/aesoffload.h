@@ -307,7 +307,12 @@ typedef struct {
                                in-place counted once); 0 = unlimited */
     int ctas;               /* resident CTAs; 0 = SM count - 4 */
     int threads;            /* CTA size, multiple of 32, 64..512; 0 = 512 (warp 0 dispatches) */
-    int tile_blocks;        /* 16-byte blocks per tile: 64, 128 or a multiple of 256; 0 = per request (~512 tiles of 64..1024 blocks) */
+    int tile_blocks;        /* 16-byte blocks per tile: 64, 128 or a multiple of 256;
+                               0 = per request (~512 tiles of 64..1024 blocks:
+                               the latency setting).  Fewer, larger tiles serve
+                               more requests per second (measured on GB300,
+                               served mix: 269 k req/s by default, 370 k with
+                               1024), at the cost of one-in-flight latency. */
     uint32_t idle_timeout_us; /* resident kernel exits after this long with no
                                  work (relaunched on the next submit); 0 = 200000 */
     int claim_mode;         /* how agents claim tiles: 0 = one global cursor
